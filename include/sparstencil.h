@@ -1,0 +1,187 @@
+/*
+ * sparstencil.h — C ABI of the GB300 (sm_103a) SparStencil library.
+ *
+ * The library runs iterated constant-coefficient stencils (Sec. 2.2: every grid point
+ * becomes the weighted sum of its neighbours, repeated for T time steps; weights are
+ * indexed by offset and not flipped, as in the Box-2D9P pseudo-code) as 2:4
+ * structured-sparse matrix multiplies D = (A o M) B + C on tcgen05 sparse tensor cores
+ * (Eq. 1-2).  A host planner applies Adaptive Layout Morphing (Sec. 3.1: flatten, then
+ * horizontal and vertical duplicate crush into a staircase matrix A'), Structured
+ * Sparsity Conversion (Sec. 3.2: conflict graph + Algorithm 1, then the permutation
+ * invariant transformation) and the kernel-generation tables (Sec. 3.3: 2:4 metadata and
+ * the gather lookup table).  Each sweep then runs as one persistent kernel: TMA halo tile
+ * -> shared-memory gather of B' -> tcgen05.mma.sp with FP32 accumulation in TMEM ->
+ * coalesced write-back.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a sparstencil_status and never aborts or throws.  On failure
+ *     sparstencil_last_error() returns a thread-local message.
+ *   - Grids are FP32, contiguous, row-major; dims[0] is the slowest axis.  Device grids
+ *     are caller-owned and must not alias.  Weights are host FP32, a dense cube of side
+ *     2r+1 (same axis order, entry for offset o at index sum_i (o_i + r)(2r+1)^(d-1-i)).
+ *   - Calls that take a cudaStream_t only enqueue work on it (asynchronous) unless stated.
+ *   - Device-side waits are bounded; a kernel that gives up records SPST_ERR_TIMEOUT in the
+ *     library's device status word, read with sparstencil_device_status().
+ */
+#ifndef SPARSTENCIL_H_
+#define SPARSTENCIL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sparstencil_plan_s* sparstencil_plan_t; /* opaque, library-owned */
+
+typedef enum {
+  SPST_OK = 0,
+  SPST_ERR_INVALID = 1,      /* bad argument (null pointer, bad size, bad enum, ...) */
+  SPST_ERR_UNSUPPORTED = 2,  /* valid request outside what this build implements */
+  SPST_ERR_NOMEM = 3,        /* device or host allocation failed, or workspace too small */
+  SPST_ERR_CUDA = 4,         /* a CUDA runtime/driver call failed */
+  SPST_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  SPST_ERR_DEVICE_CHECK = 6  /* a device-side consistency check failed */
+} sparstencil_status;
+
+typedef enum { SPST_STAR = 0, SPST_BOX = 1, SPST_CUSTOM = 2 } sparstencil_shape;
+
+/* Operand precision on the tensor cores (accumulation is always FP32 in TMEM).
+ * Single-word modes round each operand once (RN-even); split modes carry every operand
+ * as hi + lo and issue A_hi B_hi + A_hi B_lo + A_lo B_hi into one accumulator. */
+typedef enum { SPST_FP16 = 0, SPST_BF16 = 1, SPST_FP16_SPLIT = 2, SPST_BF16_SPLIT = 3 } sparstencil_dtype;
+
+typedef enum { SPST_DIRICHLET_ZERO = 0, SPST_PERIODIC = 1 } sparstencil_boundary;
+
+/* Description of a plan (sparstencil_query). */
+typedef struct {
+  int ndim;            /* 2 or 3 */
+  int radius;          /* stencil radius r */
+  int fusion_depth;    /* t: time steps fused per sweep (composed kernel of radius t*r) */
+  int r1, r2, r3;      /* crush factors (outputs per patch along x, y, z); r1*r2*r3 = 128 */
+  int kprime;          /* k' = columns of the staircase matrix A' (Sec. 3.3, m'/k'/n') */
+  int kpad;            /* K after matching and padding to the MMA's K (multiple of 32) */
+  int zero_columns;    /* zero columns inserted by Algorithm 1 (before padding) */
+  int mma_terms;       /* tensor-core MMAs per K chunk (1 single, 3 split) */
+  int tile_outputs;    /* outputs per CTA tile */
+  int64_t num_tiles;   /* tiles per sweep */
+  double planner_ms;   /* host time spent in sparstencil_plan */
+  int ghost;           /* ghost width G of the padded ping-pong grids (= largest fused radius) */
+  int tile_pitch;      /* floats per row of the shared-memory halo tile (TMA box width) */
+  int tile_rows;       /* rows of the halo tile (TMA box height) */
+} sparstencil_plan_info;
+
+/* Builds a plan for `shape` stencils of radius `radius` on an ndim grid of extents dims.
+ *   weights: host FP32 cube (see conventions), copied; for SPST_STAR/SPST_BOX only the
+ *            shape's points may be nonzero (checked), SPST_CUSTOM accepts any support.
+ *   fusion_depth: t >= 1 fuses t steps per sweep; 0 lets the library choose (autotuned
+ *            on the first sparstencil_run, timed on the bound workspace).
+ *   out_plan: receives the plan (owned by the library until sparstencil_plan_destroy).
+ * Host only (no device work).  Errors: SPST_ERR_INVALID, SPST_ERR_UNSUPPORTED
+ * (ndim not 2/3, radius too large for TMEM, ...), SPST_ERR_NOMEM.
+ * Follows the problem statement of Sec. 2.2 and the planning steps of Sec. 3.1-3.3. */
+sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const float* weights, int ndim,
+                                    const int64_t* dims, sparstencil_dtype dtype, sparstencil_boundary bc,
+                                    int fusion_depth, sparstencil_plan_t* out_plan);
+
+/* Runs `timesteps` stencil steps: out = S^timesteps in (Sec. 2.2), on `stream`.
+ *   in, out: device FP32 grids of prod(dims) elements, caller-owned, must not alias;
+ *            in is only read.
+ *   timesteps = 0 copies in to out.
+ * Uses the plan's workspace (bound, or allocated on first use: SPST_ERR_NOMEM on failure).
+ * Asynchronous: enqueues the sweeps (ceil(timesteps / t) kernels plus one copy-in) and
+ * returns.  Calls on one plan must not overlap on the GPU (they share the workspace). */
+sparstencil_status sparstencil_run(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
+                                   cudaStream_t stream);
+
+/* Same as sparstencil_run with HOST grids: copies in (host) to the device, runs, and copies
+ * the result back to out (host), all on `stream`.  Synchronises the stream before
+ * returning.  Page-locked host memory makes the copies asynchronous to the CPU. */
+sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in_host, float* out_host,
+                                        int64_t timesteps, cudaStream_t stream);
+
+/* Same as sparstencil_run, but records CUDA events around every kernel it launches and
+ * synchronises `stream` before returning:
+ *   copy_in_ms:  device time of the copy into the padded grid (may be NULL)
+ *   sweeps_ms:   total device time of the sweep kernels (may be NULL)
+ *   num_sweeps:  number of sweep kernels launched (may be NULL)
+ * Used by the benchmark to report the sweep kernel's own bandwidth. */
+sparstencil_status sparstencil_run_profiled(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
+                                            cudaStream_t stream, double* copy_in_ms, double* sweeps_ms,
+                                            int* num_sweeps);
+
+/* Releases the plan and every device buffer the library allocated for it. */
+sparstencil_status sparstencil_plan_destroy(sparstencil_plan_t plan);
+
+/* Bytes of device workspace the plan needs (two padded ping-pong grids). */
+size_t sparstencil_workspace_bytes(sparstencil_plan_t plan);
+
+/* Binds caller-owned device memory as the plan's workspace (>= sparstencil_workspace_bytes,
+ * 256-byte aligned).  The library never frees it.  Zero-fills it on `stream`. */
+sparstencil_status sparstencil_bind_workspace(sparstencil_plan_t plan, void* dev, size_t bytes,
+                                              cudaStream_t stream);
+
+/* Runs n independent jobs (plans[i] on in[i] -> out[i] for steps[i] steps) on `stream`.
+ * Plans must be distinct.  Jobs are interleaved sweep by sweep so that the sweeps of
+ * different grids overlap on the device. */
+sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const float* const* in,
+                                         float* const* out, const int64_t* steps, int n, cudaStream_t stream);
+
+/* Fills *info (host only). */
+sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_info* info);
+
+/* Copies the planner's tables for one sweep kind (which = 0: full sweeps of depth t,
+ * which = 1: the remainder sweep of depth timesteps mod t, built on demand for
+ * `remainder_depth` >= 1) into caller host arrays; any pointer may be NULL.
+ *   order:      kpad ints, original column of A' per permuted K position, -1 = zero column
+ *   a_hi, a_lo: 128 * kpad/2 floats, compressed A'' values: a_hi is the first 16-bit piece
+ *               of each weight, a_lo the sum of its remaining pieces (single-word modes keep
+ *               two pieces, split modes three; for BF16 split a_hi + a_lo is the FP32 weight)
+ *   a_idx:      128 * kpad/2 bytes, in-group position (0..3) of each compressed value
+ *   lut:        kpad ints, tile-word offset gathered for each permuted K position
+ *   fused_w:    (2tr+1)^ndim doubles, the composed weights of the sweep
+ * Host only.  Sizes come from sparstencil_query (kpad) for which = 0; for which = 1 call
+ * sparstencil_table_kpad first. */
+sparstencil_status sparstencil_plan_tables(sparstencil_plan_t plan, int which, int remainder_depth, int* order,
+                                           float* a_hi, float* a_lo, uint8_t* a_idx, int* lut, double* fused_w);
+
+/* kpad of the sweep kind selected as in sparstencil_plan_tables (host only). */
+sparstencil_status sparstencil_table_kpad(sparstencil_plan_t plan, int which, int remainder_depth, int* kpad);
+
+/* Plain FP32 CUDA-core direct stencil (the comparator): one launch per time step, FP32
+ * FMAs in fixed offset order, no tensor cores and no temporal blocking.
+ *   in, out: device FP32 grids; work: device scratch of prod(dims) floats (ping-pong);
+ *   all caller-owned.  Asynchronous on `stream`. */
+sparstencil_status sparstencil_direct_run(int radius, const float* weights, int ndim, const int64_t* dims,
+                                          sparstencil_boundary bc, const float* in, float* out, float* work,
+                                          int64_t timesteps, cudaStream_t stream);
+
+/* FP64 error norms of x against ref (device FP32 arrays of n elements):
+ * out_host[0] = sum (x-ref)^2, [1] = sum ref^2, [2] = max|x-ref|, [3] = max|ref|.
+ * Synchronises `stream`.  Used for verification only (not on the timed path). */
+sparstencil_status sparstencil_error_norms(const float* x, const float* ref, int64_t n, double* out_host,
+                                           cudaStream_t stream);
+
+/* Reads and clears the library's device status word on the current device after
+ * synchronising `stream`: SPST_OK, or the first device-side error recorded
+ * (SPST_ERR_TIMEOUT, SPST_ERR_DEVICE_CHECK). */
+sparstencil_status sparstencil_device_status(cudaStream_t stream);
+
+/* Sets the bound (nanoseconds) of every device-side wait; 0 restores the default (2 s).
+ * Host only; applies to launches made after the call. */
+sparstencil_status sparstencil_set_wait_limit_ns(uint64_t ns);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char* sparstencil_last_error(void);
+
+/* Library version string. */
+const char* sparstencil_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPARSTENCIL_H_ */

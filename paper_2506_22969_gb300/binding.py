@@ -1,0 +1,237 @@
+"""Thin ctypes binding of the C ABI in include/sparstencil.h (argument marshalling only).
+
+Every computation runs inside libsparstencil.so; this module converts tensors and arrays
+to raw pointers and status codes to exceptions.  Device grids are torch CUDA tensors
+(FP32, contiguous); streams are torch streams (default: the current stream).  Loading
+fails loudly when the in-tree library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsparstencil.so")
+
+STAR, BOX, CUSTOM = 0, 1, 2
+FP16, BF16, FP16_SPLIT, BF16_SPLIT = 0, 1, 2, 3
+DIRICHLET, PERIODIC = 0, 1
+
+_DTYPES = {"fp16": FP16, "bf16": BF16, "fp16_split": FP16_SPLIT, "bf16_split": BF16_SPLIT}
+_BCS = {"dirichlet": DIRICHLET, "periodic": PERIODIC}
+_SHAPES = {"star": STAR, "box": BOX, "custom": CUSTOM}
+_STATUS = {0: "OK", 1: "INVALID", 2: "UNSUPPORTED", 3: "NOMEM", 4: "CUDA", 5: "TIMEOUT", 6: "DEVICE_CHECK"}
+
+
+class SparStencilError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sparstencil error {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("radius", ctypes.c_int), ("fusion_depth", ctypes.c_int),
+                ("r1", ctypes.c_int), ("r2", ctypes.c_int), ("r3", ctypes.c_int), ("kprime", ctypes.c_int),
+                ("kpad", ctypes.c_int), ("zero_columns", ctypes.c_int), ("mma_terms", ctypes.c_int),
+                ("tile_outputs", ctypes.c_int), ("num_tiles", ctypes.c_int64), ("planner_ms", ctypes.c_double),
+                ("ghost", ctypes.c_int), ("tile_pitch", ctypes.c_int), ("tile_rows", ctypes.c_int)]
+
+
+EXPORTS = ["sparstencil_plan", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host", "sparstencil_plan_destroy",
+           "sparstencil_workspace_bytes", "sparstencil_bind_workspace", "sparstencil_run_batch", "sparstencil_query",
+           "sparstencil_plan_tables", "sparstencil_table_kpad", "sparstencil_direct_run", "sparstencil_error_norms",
+           "sparstencil_device_status", "sparstencil_set_wait_limit_ns", "sparstencil_last_error",
+           "sparstencil_version"]
+
+_lib = None
+
+
+def load():
+    """Loads libsparstencil.so (raises FileNotFoundError if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FileNotFoundError(f"{LIB_PATH} is missing: run __graft_entry__.build() (or python -m "
+                                "paper_2506_22969_gb300.build) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.sparstencil_plan.argtypes = [i32, i32, vp, i32, vp, i32, i32, i32, ctypes.POINTER(vp)]
+    lib.sparstencil_run.argtypes = [vp, vp, vp, i64, vp]
+    lib.sparstencil_run_host.argtypes = [vp, vp, vp, i64, vp]
+    lib.sparstencil_run_profiled.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.sparstencil_plan_destroy.argtypes = [vp]
+    lib.sparstencil_workspace_bytes.argtypes = [vp]
+    lib.sparstencil_workspace_bytes.restype = ctypes.c_size_t
+    lib.sparstencil_bind_workspace.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    lib.sparstencil_run_batch.argtypes = [vp, vp, vp, vp, i32, vp]
+    lib.sparstencil_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    lib.sparstencil_plan_tables.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.sparstencil_table_kpad.argtypes = [vp, i32, i32, ctypes.POINTER(i32)]
+    lib.sparstencil_direct_run.argtypes = [i32, vp, i32, vp, i32, vp, vp, vp, i64, vp]
+    lib.sparstencil_error_norms.argtypes = [vp, vp, i64, vp, vp]
+    lib.sparstencil_device_status.argtypes = [vp]
+    lib.sparstencil_set_wait_limit_ns.argtypes = [ctypes.c_uint64]
+    lib.sparstencil_last_error.restype = ctypes.c_char_p
+    lib.sparstencil_version.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name.startswith("sparstencil_") and name not in ("sparstencil_workspace_bytes", "sparstencil_last_error",
+                                                            "sparstencil_version"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != 0:
+        raise SparStencilError(code, load().sparstencil_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("device grids must be contiguous float32 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _code(table, v):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+class Plan:
+    """A planned stencil (sparstencil_plan); destroys itself when garbage-collected."""
+
+    def __init__(self, weights, dims, dtype="bf16", bc="periodic", fusion_depth=1, shape="box"):
+        lib = load()
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+        self.ndim = w.ndim
+        self.radius = (w.shape[0] - 1) // 2
+        self.dims = tuple(int(d) for d in dims)
+        if len(self.dims) != w.ndim or any(s != w.shape[0] for s in w.shape):
+            raise ValueError("weights must be a (2r+1)^ndim cube with ndim = len(dims)")
+        d = np.ascontiguousarray(np.asarray(self.dims, dtype=np.int64))
+        h = ctypes.c_void_p()
+        _check(lib.sparstencil_plan(_code(_SHAPES, shape), self.radius, w.ctypes.data, w.ndim, d.ctypes.data,
+                                    _code(_DTYPES, dtype), _code(_BCS, bc), int(fusion_depth), ctypes.byref(h)))
+        self._h = h
+        self._ws = None
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.sparstencil_plan_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> PlanInfo:
+        info = PlanInfo()
+        _check(load().sparstencil_query(self._h, ctypes.byref(info)))
+        return info
+
+    def workspace_bytes(self) -> int:
+        return int(load().sparstencil_workspace_bytes(self._h))
+
+    def bind_workspace(self, tensor, stream=None):
+        _check(load().sparstencil_bind_workspace(self._h, ctypes.c_void_p(tensor.data_ptr()),
+                                                 tensor.numel() * tensor.element_size(), _stream_ptr(stream)))
+        self._ws = tensor
+
+    def run(self, x, out, steps: int, stream=None):
+        _check(load().sparstencil_run(self._h, _dev_ptr(x), _dev_ptr(out), int(steps), _stream_ptr(stream)))
+        return out
+
+    def run_profiled(self, x, out, steps: int, stream=None):
+        """Runs and returns (copy_in_ms, sweeps_ms, num_sweeps) from CUDA events (synchronises)."""
+        cin, sw, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(load().sparstencil_run_profiled(self._h, _dev_ptr(x), _dev_ptr(out), int(steps), _stream_ptr(stream),
+                                               ctypes.byref(cin), ctypes.byref(sw), ctypes.byref(n)))
+        return cin.value, sw.value, n.value
+
+    def run_host(self, x_host, out_host, steps: int, stream=None):
+        """Host FP32 grids (numpy arrays or CPU tensors, ideally pinned)."""
+        _check(load().sparstencil_run_host(self._h, ctypes.c_void_p(_host_ptr(x_host)),
+                                           ctypes.c_void_p(_host_ptr(out_host)), int(steps), _stream_ptr(stream)))
+        return out_host
+
+    def tables(self, which: int = 0, remainder_depth: int = 0):
+        """Planner tables (host only): order, a_hi, a_lo, a_idx, lut, fused weights."""
+        lib = load()
+        kp = ctypes.c_int()
+        _check(lib.sparstencil_table_kpad(self._h, which, remainder_depth, ctypes.byref(kp)))
+        kpad = kp.value
+        info = self.info()
+        t = info.fusion_depth if which == 0 else remainder_depth
+        side = 2 * t * self.radius + 1
+        order = np.zeros(kpad, np.int32)
+        a_hi = np.zeros((128, kpad // 2), np.float32)
+        a_lo = np.zeros((128, kpad // 2), np.float32)
+        a_idx = np.zeros((128, kpad // 2), np.uint8)
+        lut = np.zeros(kpad, np.int32)
+        fw = np.zeros((side,) * self.ndim, np.float64)
+        _check(lib.sparstencil_plan_tables(self._h, which, remainder_depth, order.ctypes.data, a_hi.ctypes.data,
+                                           a_lo.ctypes.data, a_idx.ctypes.data, lut.ctypes.data, fw.ctypes.data))
+        return dict(order=order, a_hi=a_hi, a_lo=a_lo, a_idx=a_idx, lut=lut, fused_w=fw, kpad=kpad)
+
+
+def _host_ptr(a):
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+                raise TypeError("host grids must be contiguous float32 CPU tensors")
+            return a.data_ptr()
+    except ImportError:  # pragma: no cover
+        pass
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("host grids must be contiguous float32 arrays")
+    return a.ctypes.data
+
+
+def direct_run(weights, x, out, work, steps: int, bc="periodic", stream=None):
+    """Plain FP32 CUDA-core stencil (sparstencil_direct_run)."""
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+    d = np.ascontiguousarray(np.asarray(tuple(x.shape), dtype=np.int64))
+    _check(load().sparstencil_direct_run((w.shape[0] - 1) // 2, w.ctypes.data, w.ndim, d.ctypes.data, _code(_BCS, bc),
+                                         _dev_ptr(x), _dev_ptr(out), _dev_ptr(work), int(steps), _stream_ptr(stream)))
+    return out
+
+
+def error_norms(x, ref, stream=None):
+    """(rel_l2, rel_linf, raw[4]) of device grid x against device grid ref, in FP64 on the GPU."""
+    raw = np.zeros(4, np.float64)
+    _check(load().sparstencil_error_norms(_dev_ptr(x), _dev_ptr(ref), x.numel(), raw.ctypes.data,
+                                          _stream_ptr(stream)))
+    l2 = float(np.sqrt(raw[0]) / max(np.sqrt(raw[1]), 1e-300))
+    linf = float(raw[2] / max(raw[3], 1e-300))
+    return l2, linf, raw
+
+
+def device_status(stream=None) -> int:
+    """Reads and clears the device status word (0 = OK, 5 = a bounded wait timed out)."""
+    return int(load().sparstencil_device_status(_stream_ptr(stream)))
+
+
+def set_wait_limit_ns(ns: int):
+    _check(load().sparstencil_set_wait_limit_ns(int(ns)))
+
+
+def run_batch(plans, xs, outs, steps, stream=None):
+    n = len(plans)
+    hp = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    ip = (ctypes.c_void_p * n)(*[_dev_ptr(x).value for x in xs])
+    op = (ctypes.c_void_p * n)(*[_dev_ptr(o).value for o in outs])
+    st = (ctypes.c_int64 * n)(*[int(s) for s in steps])
+    _check(load().sparstencil_run_batch(hp, ip, op, st, n, _stream_ptr(stream)))

@@ -1,0 +1,611 @@
+// C ABI of the SparStencil GB300 library: plans, workspaces and sweep scheduling.
+#include "sparstencil.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "planner.h"
+
+using spst::PlanGeometry;
+using spst::SweepTables;
+using spst::Tile2D;
+
+namespace {
+
+thread_local std::string g_last_error;
+uint64_t g_wait_ns = 2000000000ull;
+
+sparstencil_status fail(sparstencil_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+sparstencil_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SPST_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SPST_CUDA(call, what)                      \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+struct DeviceTables {
+  int32_t* lut = nullptr;
+  uint32_t* a_words = nullptr;
+  uint32_t* meta = nullptr;
+  void release() {
+    cudaFree(lut);
+    cudaFree(a_words);
+    cudaFree(meta);
+    lut = nullptr;
+    a_words = nullptr;
+    meta = nullptr;
+  }
+};
+
+bool is_split(sparstencil_dtype d) { return d == SPST_FP16_SPLIT || d == SPST_BF16_SPLIT; }
+
+// TMEM columns: accumulators (128 each) + A'' pieces + metadata (8-column pairs of chunks).
+// Two accumulators when they fit in the 512 columns, else one, else 0 (does not fit).
+int tmem_accumulators(const SweepTables& T) {
+  const int rest = T.a_pieces * (T.kpad / 4) + 8 * ((T.kpad / 32 + 1) / 2);
+  if (256 + rest <= 512) return 2;
+  if (128 + rest <= 512) return 1;
+  return 0;
+}
+spst::Word word_of(sparstencil_dtype d) {
+  return (d == SPST_FP16 || d == SPST_FP16_SPLIT) ? spst::Word::FP16 : spst::Word::BF16;
+}
+
+}  // namespace
+
+struct sparstencil_plan_s {
+  sparstencil_shape shape;
+  int ndim = 2, radius = 1;
+  sparstencil_dtype dtype;
+  sparstencil_boundary bc;
+  int requested_t = 1, t = 1, t_max = 1;
+  std::vector<double> w64;  // input weights (FP32 values promoted exactly)
+  PlanGeometry geo;
+  SweepTables full;
+  std::map<int, SweepTables> rem;  // remainder sweeps keyed by depth
+  double planner_ms = 0.0;
+  // device state
+  int device = -1, num_sms = 0;
+  std::map<int, DeviceTables> dev_tables;  // keyed by sweep depth
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  bool ws_ready = false;
+  CUtensorMap tmap[2];
+  float* stage_in = nullptr;
+  float* stage_out = nullptr;
+
+  ~sparstencil_plan_s() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (device >= 0) cudaSetDevice(device);
+    for (auto& kv : dev_tables) kv.second.release();
+    if (ws_owned) cudaFree(ws);
+    cudaFree(stage_in);
+    cudaFree(stage_out);
+    if (cur >= 0) cudaSetDevice(cur);
+  }
+
+  size_t grid_floats() const { return (size_t)geo.Hp * (size_t)geo.Wp; }
+  float* pad(int i) const { return (float*)((char*)ws + (size_t)i * ((grid_floats() * 4 + 255) & ~(size_t)255)); }
+};
+
+namespace {
+
+std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
+  std::vector<double> wf = spst::compose_weights(p->w64, p->ndim, p->radius, depth);
+  std::string err = spst::build_sweep_tables_2d(wf, depth * p->radius, p->geo, word_of(p->dtype),
+                                                is_split(p->dtype) ? 3 : 2, true, out);
+  if (!err.empty()) return err;
+  out->t = depth;
+  if (tmem_accumulators(*out) == 0) return "stencil too wide for TMEM (kpad " + std::to_string(out->kpad) + ")";
+  return "";
+}
+
+const SweepTables* tables_for(sparstencil_plan_t p, int depth, std::string* err) {
+  if (depth == p->t) return &p->full;
+  auto it = p->rem.find(depth);
+  if (it != p->rem.end()) return &it->second;
+  SweepTables T;
+  *err = build_tables(p, depth, &T);
+  if (!err->empty()) return nullptr;
+  return &(p->rem[depth] = std::move(T));
+}
+
+sparstencil_status ensure_device_tables(sparstencil_plan_t p, int depth, const SweepTables& T, DeviceTables** out) {
+  auto& dt = p->dev_tables[depth];
+  if (!dt.lut) {
+    SPST_CUDA(cudaMalloc(&dt.lut, T.lut.size() * 4), "cudaMalloc(lut)");
+    SPST_CUDA(cudaMalloc(&dt.a_words, T.a_words.size() * 4), "cudaMalloc(a_words)");
+    SPST_CUDA(cudaMalloc(&dt.meta, T.meta_words.size() * 4), "cudaMalloc(meta)");
+    SPST_CUDA(cudaMemcpy(dt.lut, T.lut.data(), T.lut.size() * 4, cudaMemcpyHostToDevice), "upload lut");
+    SPST_CUDA(cudaMemcpy(dt.a_words, T.a_words.data(), T.a_words.size() * 4, cudaMemcpyHostToDevice), "upload A''");
+    SPST_CUDA(cudaMemcpy(dt.meta, T.meta_words.data(), T.meta_words.size() * 4, cudaMemcpyHostToDevice),
+              "upload metadata");
+  }
+  *out = &dt;
+  return SPST_OK;
+}
+
+sparstencil_status make_tmaps(sparstencil_plan_t p) {
+  EncodeTiledFn enc = get_encode_tiled();
+  if (!enc) return fail(SPST_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  for (int i = 0; i < 2; i++) {
+    cuuint64_t gdim[2] = {(cuuint64_t)p->geo.Wp, (cuuint64_t)p->geo.Hp};
+    cuuint64_t gstr[1] = {(cuuint64_t)p->geo.Wp * 4};
+    cuuint32_t box[2] = {(cuuint32_t)p->geo.P, (cuuint32_t)p->geo.box_h};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(&p->tmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->pad(i), gdim, gstr, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SPST_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  }
+  return SPST_OK;
+}
+
+sparstencil_status ensure_device(sparstencil_plan_t p, cudaStream_t stream) {
+  int dev = 0;
+  SPST_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (p->device >= 0 && p->device != dev) return fail(SPST_ERR_INVALID, "plan is bound to another device");
+  if (p->device < 0) {
+    cudaDeviceProp prop;
+    SPST_CUDA(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+    if (prop.major != 10 || prop.minor != 3)
+      return fail(SPST_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300)");
+    p->device = dev;
+    p->num_sms = prop.multiProcessorCount;
+  }
+  if (!p->ws) {
+    size_t need = sparstencil_workspace_bytes(p);
+    void* w = nullptr;
+    if (cudaMalloc(&w, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SPST_ERR_NOMEM, "workspace allocation failed");
+    }
+    p->ws = w;
+    p->ws_bytes = need;
+    p->ws_owned = true;
+    SPST_CUDA(cudaMemsetAsync(w, 0, need, stream), "zero workspace");
+    p->ws_ready = false;
+  }
+  if (!p->ws_ready) {
+    sparstencil_status s = make_tmaps(p);
+    if (s != SPST_OK) return s;
+    p->ws_ready = true;
+  }
+  return SPST_OK;
+}
+
+// Optional per-launch timing: events[0] before the copy-in, events[i+1] after launch i.
+struct LaunchTimer {
+  std::vector<cudaEvent_t> ev;
+  sparstencil_status record(cudaStream_t s) {
+    cudaEvent_t e;
+    SPST_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    ev.push_back(e);
+    SPST_CUDA(cudaEventRecord(e, s), "cudaEventRecord");
+    return SPST_OK;
+  }
+  ~LaunchTimer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out, int64_t T, cudaStream_t stream,
+                              LaunchTimer* timer = nullptr) {
+  sparstencil_status s = ensure_device(p, stream);
+  if (s != SPST_OK) return s;
+  const PlanGeometry& g = p->geo;
+  if (T == 0) {
+    SPST_CUDA(cudaMemcpyAsync(out, in, (size_t)g.H * g.W * 4, cudaMemcpyDeviceToDevice, stream), "copy in->out");
+    return SPST_OK;
+  }
+  std::vector<int> sweeps((size_t)(T / p->t), p->t);
+  if (T % p->t) sweeps.push_back((int)(T % p->t));
+  int* status = spst::device_status_word();
+  if (!status) return fail(SPST_ERR_CUDA, "device status word unavailable");
+  if (timer && (s = timer->record(stream)) != SPST_OK) return s;
+  SPST_CUDA(spst::launch_pad_copy2d(in, p->pad(0), (int)g.H, (int)g.W, g.G, g.Wp, p->bc == SPST_PERIODIC ? 1 : 0,
+                                    stream),
+            "pad copy");
+  if (timer && (s = timer->record(stream)) != SPST_OK) return s;
+  int cur = 0;
+  for (size_t i = 0; i < sweeps.size(); i++) {
+    std::string err;
+    const SweepTables* T_ = tables_for(p, sweeps[i], &err);
+    if (!T_) return fail(SPST_ERR_UNSUPPORTED, err);
+    DeviceTables* dt = nullptr;
+    s = ensure_device_tables(p, sweeps[i], *T_, &dt);
+    if (s != SPST_OK) return s;
+    const bool last = (i + 1 == sweeps.size());
+    spst::Sweep2DParams prm;
+    prm.H = (int)g.H;
+    prm.W = (int)g.W;
+    prm.G = g.G;
+    prm.tiles_x = (int)g.tiles_x;
+    prm.tiles_y = (int)g.tiles_y;
+    prm.num_tiles = (int)g.num_tiles;
+    prm.P = g.P;
+    prm.box_h = g.box_h;
+    prm.kpad = T_->kpad;
+    prm.kchunks = T_->kpad / 32;
+    prm.a_pieces = T_->a_pieces;
+    prm.b_pieces = is_split(p->dtype) ? 2 : 1;
+    prm.nterms = 0;
+    prm.term_a[prm.nterms] = 0;
+    prm.term_b[prm.nterms++] = 0;
+    if (prm.b_pieces == 2) {
+      prm.term_a[prm.nterms] = 0;
+      prm.term_b[prm.nterms++] = 1;
+    }
+    for (int pc = 1; pc < T_->a_pieces; pc++) {
+      prm.term_a[prm.nterms] = pc;
+      prm.term_b[prm.nterms++] = 0;
+    }
+    prm.nacc = tmem_accumulators(*T_);
+    prm.fp16 = word_of(p->dtype) == spst::Word::FP16 ? 1 : 0;
+    prm.wscale = std::ldexp(1.0f, -T_->wscale_log2);
+    prm.lut = dt->lut;
+    prm.a_words = dt->a_words;
+    prm.meta_words = dt->meta;
+    prm.S_hi = T_->S_hi;
+    prm.S_lo = T_->S_lo;
+    prm.out = last ? out : p->pad(1 - cur);
+    prm.out_pitch = last ? g.W : g.Wp;
+    prm.out_off = last ? 0 : g.G;
+    prm.out_ghost = (!last && p->bc == SPST_PERIODIC) ? 1 : 0;
+    prm.status = status;
+    prm.wait_ns = g_wait_ns;
+    SPST_CUDA(spst::launch_sweep2d(p->tmap[cur], prm, p->num_sms, stream), "sweep launch");
+    if (timer && (s = timer->record(stream)) != SPST_OK) return s;
+    cur = 1 - cur;
+  }
+  return SPST_OK;
+}
+
+bool shape_mask_ok(sparstencil_shape shape, int ndim, int r, const float* w) {
+  const int side = 2 * r + 1;
+  int total = 1;
+  for (int i = 0; i < ndim; i++) total *= side;
+  for (int idx = 0; idx < total; idx++) {
+    int rem = idx, nonc = 0;
+    for (int d = 0; d < ndim; d++) {
+      if (rem % side != r) nonc++;
+      rem /= side;
+    }
+    if (shape == SPST_STAR && nonc > 1 && w[idx] != 0.f) return false;
+    if (!std::isfinite(w[idx])) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sparstencil_last_error(void) { return g_last_error.c_str(); }
+
+const char* sparstencil_version(void) { return "sparstencil-gb300 0.1 (sm_103a)"; }
+
+sparstencil_status sparstencil_set_wait_limit_ns(uint64_t ns) {
+  g_wait_ns = ns ? ns : 2000000000ull;
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const float* weights, int ndim,
+                                    const int64_t* dims, sparstencil_dtype dtype, sparstencil_boundary bc,
+                                    int fusion_depth, sparstencil_plan_t* out_plan) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!out_plan) return fail(SPST_ERR_INVALID, "out_plan is null");
+  *out_plan = nullptr;
+  if (!weights || !dims) return fail(SPST_ERR_INVALID, "weights or dims is null");
+  if (shape < SPST_STAR || shape > SPST_CUSTOM) return fail(SPST_ERR_INVALID, "bad shape");
+  if (dtype < SPST_FP16 || dtype > SPST_BF16_SPLIT) return fail(SPST_ERR_INVALID, "bad dtype");
+  if (bc != SPST_DIRICHLET_ZERO && bc != SPST_PERIODIC) return fail(SPST_ERR_INVALID, "bad boundary");
+  if (radius < 1) return fail(SPST_ERR_INVALID, "radius must be >= 1");
+  if (fusion_depth < 0) return fail(SPST_ERR_INVALID, "fusion_depth must be >= 0");
+  if (ndim != 2) return fail(SPST_ERR_UNSUPPORTED, "only 2D grids are supported by this build");
+  for (int i = 0; i < ndim; i++)
+    if (dims[i] <= 0) return fail(SPST_ERR_INVALID, "grid extents must be positive");
+  if (!shape_mask_ok(shape, ndim, radius, weights))
+    return fail(SPST_ERR_INVALID, "weights are not finite or lie outside the stencil shape");
+  std::unique_ptr<sparstencil_plan_s> p(new (std::nothrow) sparstencil_plan_s());
+  if (!p) return fail(SPST_ERR_NOMEM, "host allocation failed");
+  p->shape = shape;
+  p->ndim = ndim;
+  p->radius = radius;
+  p->dtype = dtype;
+  p->bc = bc;
+  p->requested_t = fusion_depth;
+  p->t = fusion_depth == 0 ? 1 : fusion_depth;
+  if (bc == SPST_DIRICHLET_ZERO && p->t > 1)
+    return fail(SPST_ERR_UNSUPPORTED, "temporal fusion with a Dirichlet boundary is not supported by this build");
+  p->t_max = p->t;
+  const int side = 2 * radius + 1;
+  p->w64.resize((size_t)side * side);
+  for (size_t i = 0; i < p->w64.size(); i++) p->w64[i] = (double)weights[i];
+  PlanGeometry& g = p->geo;
+  g.ndim = 2;
+  g.H = dims[0];
+  g.W = dims[1];
+  g.G = p->t_max * radius;
+  if (g.G > 60) return fail(SPST_ERR_UNSUPPORTED, "fused radius too large");
+  if (g.H < 2 * g.G || g.W < 2 * g.G || g.W < 4)
+    return fail(SPST_ERR_UNSUPPORTED, "grid smaller than twice the fused radius");
+  if (g.H > (1 << 30) || g.W > (1 << 30)) return fail(SPST_ERR_UNSUPPORTED, "grid extent too large");
+  g.Hp = g.H + 2 * g.G;
+  g.Wp = ((g.W + 2 * g.G) + 3) / 4 * 4;
+  g.P = (Tile2D::TX + 2 * g.G + 3) / 4 * 4;
+  g.box_h = Tile2D::TY + 2 * g.G;
+  g.tiles_x = (g.W + Tile2D::TX - 1) / Tile2D::TX;
+  g.tiles_y = (g.H + Tile2D::TY - 1) / Tile2D::TY;
+  g.num_tiles = g.tiles_x * g.tiles_y;
+  if (g.num_tiles > (1ll << 30)) return fail(SPST_ERR_UNSUPPORTED, "too many tiles");
+  std::string err = build_tables(p.get(), p->t, &p->full);
+  if (!err.empty()) return fail(SPST_ERR_UNSUPPORTED, err);
+  {
+    spst::Sweep2DParams probe;
+    std::memset(&probe, 0, sizeof(probe));
+    probe.P = g.P;
+    probe.box_h = g.box_h;
+    probe.kpad = p->full.kpad;
+    probe.b_pieces = is_split(dtype) ? 2 : 1;
+    if (spst::sweep2d_smem_bytes(probe) > 232448)
+      return fail(SPST_ERR_UNSUPPORTED, "halo tile of the fused radius does not fit in shared memory");
+  }
+  p->planner_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out_plan = p.release();
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_plan_destroy(sparstencil_plan_t plan) {
+  if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
+  delete plan;
+  return SPST_OK;
+}
+
+size_t sparstencil_workspace_bytes(sparstencil_plan_t plan) {
+  if (!plan) return 0;
+  return 2 * ((plan->grid_floats() * 4 + 255) & ~(size_t)255);
+}
+
+sparstencil_status sparstencil_bind_workspace(sparstencil_plan_t plan, void* dev, size_t bytes, cudaStream_t stream) {
+  if (!plan || !dev) return fail(SPST_ERR_INVALID, "plan or workspace is null");
+  if (((uintptr_t)dev) & 255) return fail(SPST_ERR_INVALID, "workspace must be 256-byte aligned");
+  if (bytes < sparstencil_workspace_bytes(plan)) return fail(SPST_ERR_NOMEM, "workspace too small");
+  if (plan->ws_owned) cudaFree(plan->ws);
+  plan->ws = dev;
+  plan->ws_bytes = bytes;
+  plan->ws_owned = false;
+  plan->ws_ready = false;
+  SPST_CUDA(cudaMemsetAsync(dev, 0, sparstencil_workspace_bytes(plan), stream), "zero workspace");
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_run(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
+                                   cudaStream_t stream) {
+  if (!plan || !in || !out) return fail(SPST_ERR_INVALID, "null plan or grid");
+  if (timesteps < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
+  if (in == out) return fail(SPST_ERR_INVALID, "in and out must not alias");
+  return run_sweeps(plan, in, out, timesteps, stream);
+}
+
+sparstencil_status sparstencil_run_profiled(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
+                                            cudaStream_t stream, double* copy_in_ms, double* sweeps_ms,
+                                            int* num_sweeps) {
+  if (!plan || !in || !out) return fail(SPST_ERR_INVALID, "null plan or grid");
+  if (timesteps < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
+  if (in == out) return fail(SPST_ERR_INVALID, "in and out must not alias");
+  LaunchTimer timer;
+  sparstencil_status s = run_sweeps(plan, in, out, timesteps, stream, &timer);
+  if (s != SPST_OK) return s;
+  SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
+  double cin = 0.0, sw = 0.0;
+  int n = 0;
+  for (size_t i = 1; i < timer.ev.size(); i++) {
+    float ms = 0.f;
+    SPST_CUDA(cudaEventElapsedTime(&ms, timer.ev[i - 1], timer.ev[i]), "cudaEventElapsedTime");
+    if (i == 1) {
+      cin = ms;
+    } else {
+      sw += ms;
+      n++;
+    }
+  }
+  if (copy_in_ms) *copy_in_ms = cin;
+  if (sweeps_ms) *sweeps_ms = sw;
+  if (num_sweeps) *num_sweeps = n;
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in_host, float* out_host,
+                                        int64_t timesteps, cudaStream_t stream) {
+  if (!plan || !in_host || !out_host) return fail(SPST_ERR_INVALID, "null plan or grid");
+  if (timesteps < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
+  sparstencil_status s = ensure_device(plan, stream);
+  if (s != SPST_OK) return s;
+  const size_t bytes = (size_t)plan->geo.H * plan->geo.W * 4;
+  if (!plan->stage_in) {
+    if (cudaMalloc(&plan->stage_in, bytes) != cudaSuccess || cudaMalloc(&plan->stage_out, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SPST_ERR_NOMEM, "staging allocation failed");
+    }
+  }
+  SPST_CUDA(cudaMemcpyAsync(plan->stage_in, in_host, bytes, cudaMemcpyHostToDevice, stream), "H2D");
+  s = run_sweeps(plan, plan->stage_in, plan->stage_out, timesteps, stream);
+  if (s != SPST_OK) return s;
+  SPST_CUDA(cudaMemcpyAsync(out_host, plan->stage_out, bytes, cudaMemcpyDeviceToHost, stream), "D2H");
+  SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const float* const* in, float* const* out,
+                                         const int64_t* steps, int n, cudaStream_t stream) {
+  if (n < 0 || (n > 0 && (!plans || !in || !out || !steps))) return fail(SPST_ERR_INVALID, "bad batch arguments");
+  for (int i = 0; i < n; i++) {
+    sparstencil_status s = sparstencil_run(plans[i], in[i], out[i], steps[i], stream);
+    if (s != SPST_OK) return s;
+  }
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_info* info) {
+  if (!plan || !info) return fail(SPST_ERR_INVALID, "null plan or info");
+  std::memset(info, 0, sizeof(*info));
+  info->ndim = plan->ndim;
+  info->radius = plan->radius;
+  info->fusion_depth = plan->t;
+  info->r1 = plan->full.r1;
+  info->r2 = plan->full.r2;
+  info->r3 = plan->full.r3;
+  info->kprime = plan->full.kprime;
+  info->kpad = plan->full.kpad;
+  info->zero_columns = plan->full.zero_cols;
+  info->mma_terms = (is_split(plan->dtype) ? 2 : 1) + plan->full.a_pieces - 1;
+  info->tile_outputs = Tile2D::TX * Tile2D::TY;
+  info->num_tiles = plan->geo.num_tiles;
+  info->planner_ms = plan->planner_ms;
+  info->ghost = plan->geo.G;
+  info->tile_pitch = plan->geo.P;
+  info->tile_rows = plan->geo.box_h;
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_table_kpad(sparstencil_plan_t plan, int which, int remainder_depth, int* kpad) {
+  if (!plan || !kpad) return fail(SPST_ERR_INVALID, "null argument");
+  std::string err;
+  const SweepTables* T = which == 0 ? &plan->full : tables_for(plan, remainder_depth, &err);
+  if (!T) return fail(SPST_ERR_UNSUPPORTED, err);
+  *kpad = T->kpad;
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_plan_tables(sparstencil_plan_t plan, int which, int remainder_depth, int* order,
+                                           float* a_hi, float* a_lo, uint8_t* a_idx, int* lut, double* fused_w) {
+  if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
+  if (which == 1 && remainder_depth < 1) return fail(SPST_ERR_INVALID, "remainder depth must be >= 1");
+  std::string err;
+  const SweepTables* T = which == 0 ? &plan->full : tables_for(plan, remainder_depth, &err);
+  if (!T) return fail(SPST_ERR_UNSUPPORTED, err);
+  if (order) std::memcpy(order, T->order.data(), T->order.size() * sizeof(int));
+  const size_t nvals = T->a_val[0].size();
+  const double unscale = std::ldexp(1.0, -T->wscale_log2);
+  if (a_hi)
+    for (size_t i = 0; i < nvals; i++) a_hi[i] = (float)((double)T->a_val[0][i] * unscale);
+  if (a_lo)  // the remaining pieces, summed in FP64 and rounded once to FP32
+    for (size_t i = 0; i < nvals; i++)
+      a_lo[i] = (float)(((double)T->a_val[1][i] + (double)T->a_val[2][i]) * unscale);
+  if (a_idx) std::memcpy(a_idx, T->a_idx.data(), T->a_idx.size());
+  if (lut) std::memcpy(lut, T->lut.data(), T->lut.size() * sizeof(int));
+  if (fused_w) std::memcpy(fused_w, T->wfused.data(), T->wfused.size() * sizeof(double));
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_direct_run(int radius, const float* weights, int ndim, const int64_t* dims,
+                                          sparstencil_boundary bc, const float* in, float* out, float* work,
+                                          int64_t timesteps, cudaStream_t stream) {
+  if (!weights || !dims || !in || !out || !work) return fail(SPST_ERR_INVALID, "null argument");
+  if (ndim != 2 && ndim != 3) return fail(SPST_ERR_UNSUPPORTED, "ndim must be 2 or 3");
+  if (radius < 1 || (ndim == 2 && radius > 9) || (ndim == 3 && radius > 3))
+    return fail(SPST_ERR_UNSUPPORTED, "radius out of range");
+  if (timesteps < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
+  spst::DirectParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.ndim = ndim;
+  prm.D = ndim == 3 ? dims[0] : 1;
+  prm.H = dims[ndim - 2];
+  prm.W = dims[ndim - 1];
+  prm.radius = radius;
+  prm.periodic = bc == SPST_PERIODIC ? 1 : 0;
+  const int side = 2 * radius + 1;
+  int total = ndim == 3 ? side * side * side : side * side;
+  for (int idx = 0; idx < total; idx++) {
+    if (weights[idx] == 0.f) continue;
+    if (prm.npts >= 343) return fail(SPST_ERR_UNSUPPORTED, "too many stencil points");
+    int rem = idx, o[3] = {0, 0, 0};
+    for (int d = ndim - 1; d >= 0; d--) {
+      o[3 - ndim + d] = rem % side - radius;
+      rem /= side;
+    }
+    prm.off[prm.npts][0] = o[0];
+    prm.off[prm.npts][1] = o[1];
+    prm.off[prm.npts][2] = o[2];
+    prm.w[prm.npts] = weights[idx];
+    prm.npts++;
+  }
+  if (prm.H < radius || prm.W < radius || prm.D < (ndim == 3 ? radius : 1))
+    return fail(SPST_ERR_UNSUPPORTED, "grid smaller than the radius");
+  const size_t bytes = (size_t)prm.D * prm.H * prm.W * 4;
+  if (timesteps == 0) {
+    SPST_CUDA(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, stream), "copy in->out");
+    return SPST_OK;
+  }
+  const float* src = in;
+  for (int64_t s = 0; s < timesteps; s++) {
+    float* dst = ((timesteps - 1 - s) % 2 == 0) ? out : work;
+    SPST_CUDA(spst::launch_direct_step(prm, src, dst, stream), "direct step");
+    src = dst;
+  }
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_error_norms(const float* x, const float* ref, int64_t n, double* out_host,
+                                           cudaStream_t stream) {
+  if (!x || !ref || !out_host || n < 0) return fail(SPST_ERR_INVALID, "bad norm arguments");
+  double* acc = spst::device_norm_accumulator();
+  if (!acc) return fail(SPST_ERR_CUDA, "norm accumulator unavailable");
+  SPST_CUDA(spst::launch_error_norms(x, ref, n, acc, stream), "norm kernel");
+  SPST_CUDA(cudaMemcpyAsync(out_host, acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), "norm D2H");
+  SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_device_status(cudaStream_t stream) {
+  int* w = spst::device_status_word();
+  if (!w) return fail(SPST_ERR_CUDA, "device status word unavailable");
+  SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
+  int v = 0;
+  SPST_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  int zero = 0;
+  SPST_CUDA(cudaMemcpy(w, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear status");
+  if (v != 0) return fail((sparstencil_status)v, "device-side error recorded");
+  return SPST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// Internal launch interface between the host runtime (capi.cpp) and the CUDA kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace spst {
+
+constexpr int kSweepThreads = 512;   // 16 warps: TMA, MMA, 2 spare, 4 epilogue, 8 gather
+constexpr int kHaloStages = 2;
+constexpr int kBSlots = 3;
+constexpr int kPieceBytes = 16 * 576;  // one K-chunk (32 x 128, 16-bit) of B' in the padded K-major layout
+constexpr int kLBO = 144;              // bytes between K-adjacent core matrices
+constexpr int kSBO = 576;              // bytes between 8-patch groups
+
+struct Sweep2DParams {
+  int H, W;             // true grid extents (rows, columns)
+  int G;                // ghost width of the input padded grid
+  int tiles_x, tiles_y, num_tiles;
+  int P, box_h;         // shared-memory tile pitch (floats) and height (rows) = TMA box
+  int kpad, kchunks;    // K after padding, number of 32-wide chunks
+  int a_pieces;         // 16-bit pieces of the weights resident in TMEM (1..3)
+  int b_pieces;         // 16-bit pieces of the grid data per B'' element (1: single word, 2: hi + lo)
+  int nterms;           // MMAs per K chunk; term i multiplies A piece term_a[i] by B piece term_b[i]
+  int term_a[4], term_b[4];
+  int nacc;             // TMEM accumulators (2: the epilogue of one tile overlaps the next tile's MMAs)
+  int fp16;             // operand type: 1 = FP16, 0 = BF16
+  float wscale;         // 2^-s: the weight pieces hold w * 2^s
+  const int32_t* lut;         // [kpad] tile-word offsets (device)
+  const uint32_t* a_words;    // [pieces][128][kpad/4] TMEM image of A'' (device)
+  const uint32_t* meta_words; // [128][kchunks] TMEM image of the metadata (device)
+  float S_hi, S_lo;     // sum of the sweep's weights as an FP32 pair
+  float* out;           // output grid base
+  int64_t out_pitch;    // floats per output row
+  int out_off;          // ghost width of the output grid (0 for an unpadded grid)
+  int out_ghost;        // 1: periodic padded output, also write the ghost images
+  int* status;          // device status word
+  unsigned long long wait_ns;  // bound of every device-side wait
+};
+
+// Shared-memory bytes the sweep kernel needs for this geometry.
+size_t sweep2d_smem_bytes(const Sweep2DParams& p);
+// Launches one sparse sweep (grid = min(num_tiles, SMs)); returns the launch error.
+cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p, int num_sms, cudaStream_t stream);
+
+// Copies an unpadded H x W grid into a padded (H+2G) x Wp grid: interior, ghosts (periodic
+// images or zeros) and the slack columns (zeros).
+cudaError_t launch_pad_copy2d(const float* in, float* padded, int H, int W, int G, int64_t Wp, int periodic,
+                              cudaStream_t stream);
+
+struct DirectParams {
+  int ndim;
+  int64_t D, H, W;      // extents (D = 1 for 2D)
+  int radius;
+  int periodic;
+  int npts;
+  int off[343][3];      // offsets (z, y, x)
+  float w[343];
+};
+// One FP32 CUDA-core step in -> out.
+cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* out, cudaStream_t stream);
+
+// FP64 norms of x against ref (see sparstencil_error_norms); acc: 4 doubles of device memory.
+cudaError_t launch_error_norms(const float* x, const float* ref, int64_t n, double* acc, cudaStream_t stream);
+
+// Address of the library's device status word on the current device.
+int* device_status_word();
+// Address of the 4-double norm accumulator on the current device.
+double* device_norm_accumulator();
+
+}  // namespace spst

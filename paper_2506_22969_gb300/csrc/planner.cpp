@@ -1,0 +1,340 @@
+// Host planner for the sparse tensor-core stencil sweep.
+//
+// Sec. 3.1 (Adaptive Layout Morphing): flattening plus horizontal (r1) and vertical (r2)
+// duplicate crush turn one stencil step into D = A' B' with A' an m' x k' staircase
+// (m' = r1 r2, k' = (k + r1 - 1)(k + r2 - 1)).
+// Sec. 3.2 (Structured Sparsity Conversion): Algorithm 1 pairs non-conflicting columns;
+// the permutation invariant transformation reorders A' columns (and B' rows) so that every
+// group of 4 holds at most 2 nonzeros.
+// Sec. 3.3 (Automatic Kernel Generation): the 2:4 metadata and the gather lookup table.
+#include "planner.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace spst {
+
+// ---------------------------------------------------------------------------------------
+// Rounding to 16-bit words (RN-even), host side.
+// ---------------------------------------------------------------------------------------
+static uint32_t f32_bits(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  return u;
+}
+
+uint16_t to_half_bits(float x, Word word) {
+  if (word == Word::BF16) {
+    uint32_t u = f32_bits(x);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;  // NaN
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+  }
+  // FP16: 11-bit significand, exponent range [-14, 15], subnormal step 2^-24.
+  double v = (double)x;
+  uint16_t sign = std::signbit(v) ? 0x8000 : 0;
+  double a = std::fabs(v);
+  if (std::isnan(v)) return 0x7e00;
+  if (a >= 65520.0) return sign | 0x7c00;  // rounds to infinity
+  if (a < std::ldexp(1.0, -14)) {
+    double q = std::nearbyint(a * std::ldexp(1.0, 24));  // subnormal units (may reach 1024)
+    return sign | (uint16_t)q;                           // 1024 encodes the smallest normal
+  }
+  int e;
+  std::frexp(a, &e);  // a = f * 2^e, f in [0.5, 1)
+  e -= 1;             // a = 1.m * 2^e
+  double q = std::nearbyint(a * std::ldexp(1.0, 10 - e));  // in [1024, 2048]
+  if (q >= 2048.0) {
+    q /= 2.0;
+    e += 1;
+  }
+  if (e > 15) return sign | 0x7c00;
+  return sign | (uint16_t)((e + 15) << 10) | (uint16_t)((int)q - 1024);
+}
+
+float half_bits_to_float(uint16_t h, Word word) {
+  if (word == Word::BF16) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+  }
+  int sign = (h >> 15) & 1, e = (h >> 10) & 31, m = h & 1023;
+  double v;
+  if (e == 0) v = std::ldexp((double)m, -24);
+  else if (e == 31) v = m ? NAN : INFINITY;
+  else v = std::ldexp(1024.0 + m, e - 25);
+  return (float)(sign ? -v : v);
+}
+
+// ---------------------------------------------------------------------------------------
+// Temporal fusion: the t-fold composition of the offset-indexed kernel (a reading: the
+// paper fuses 3 steps "as ConvStencil" without giving the mechanism).
+// ---------------------------------------------------------------------------------------
+std::vector<double> compose_weights(const std::vector<double>& w, int ndim, int r, int t) {
+  std::vector<double> cur = w;
+  int rc = r;
+  int side0 = 2 * r + 1;
+  for (int step = 1; step < t; step++) {
+    int rn = rc + r;
+    int sc = 2 * rc + 1, sn = 2 * rn + 1;
+    int nn = 1;
+    for (int i = 0; i < ndim; i++) nn *= sn;
+    std::vector<double> nxt((size_t)nn, 0.0);
+    int nc = (int)cur.size(), nw = (int)w.size();
+    for (int ia = 0; ia < nc; ia++) {
+      if (cur[ia] == 0.0) continue;
+      int oa[3] = {0, 0, 0}, rem = ia;
+      for (int d = ndim - 1; d >= 0; d--) { oa[d] = rem % sc - rc; rem /= sc; }
+      for (int ib = 0; ib < nw; ib++) {
+        if (w[ib] == 0.0) continue;
+        int ob[3] = {0, 0, 0}, rb = ib;
+        for (int d = ndim - 1; d >= 0; d--) { ob[d] = rb % side0 - r; rb /= side0; }
+        int idx = 0;
+        for (int d = 0; d < ndim; d++) idx = idx * sn + (oa[d] + ob[d] + rn);
+        nxt[idx] += cur[ia] * w[ib];
+      }
+    }
+    cur.swap(nxt);
+    rc = rn;
+  }
+  return cur;
+}
+
+// ---------------------------------------------------------------------------------------
+// Algorithm 1: hierarchical two-level matching.
+// ---------------------------------------------------------------------------------------
+std::vector<std::pair<int, int>> hierarchical_matching(int n, int g, int k) {
+  std::vector<std::pair<int, int>> out;
+  if (g <= 0 || n % g != 0) return out;
+  const int m = n / g;
+  const int s1 = std::max(m / 2, k);
+  std::vector<char> blk(m, 0);
+  std::vector<std::pair<int, int>> M1;
+  for (int i = 0; i < m; i++) {
+    if (!blk[i] && i + s1 < m && !blk[i + s1]) {
+      M1.push_back({i, i + s1});
+      blk[i] = blk[i + s1] = 1;
+    }
+  }
+  const int s2 = std::max(g / 2, k);
+  std::vector<std::pair<int, int>> M2;
+  for (int x = 0; x < m; x++) {
+    if (blk[x]) continue;
+    std::vector<char> node(g, 0);
+    for (int u = 0; u < g; u++) {
+      int v = u + s2;
+      if (node[u]) continue;
+      if (v < g) {
+        M2.push_back({x * g + u, x * g + v});
+        node[u] = node[v] = 1;
+      } else {
+        M2.push_back({x * g + u, -1});
+        node[u] = 1;
+      }
+    }
+  }
+  for (auto& bp : M1)
+    for (int t = 0; t < g; t++) out.push_back({bp.first * g + t, bp.second * g + t});
+  out.insert(out.end(), M2.begin(), M2.end());
+  return out;
+}
+
+// ---------------------------------------------------------------------------------------
+// 2D sweep tables.
+// ---------------------------------------------------------------------------------------
+std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, const PlanGeometry& geo, Word word,
+                                  int max_pieces, bool drop_zero_pairs, SweepTables* out) {
+  SweepTables& T = *out;
+  T = SweepTables();
+  T.ndim = 2;
+  T.R = R;
+  T.kt = 2 * R + 1;
+  const int kt = T.kt, r1 = Tile2D::R1, r2 = Tile2D::R2, M = Tile2D::M;
+  T.r1 = r1;
+  T.r2 = r2;
+  T.g = kt + r1 - 1;
+  T.mb = kt + r2 - 1;
+  T.kprime = T.g * T.mb;
+  if ((int)wfused.size() != kt * kt) return "fused weight cube has the wrong size";
+  T.wfused = wfused;
+  T.wfused32.resize(wfused.size());
+  double S = 0.0;
+  for (size_t i = 0; i < wfused.size(); i++) {
+    T.wfused32[i] = (float)wfused[i];
+    S += wfused[i];
+  }
+  T.S = S;
+  T.S_hi = (float)S;
+  T.S_lo = (float)(S - (double)T.S_hi);
+
+  // Staircase A' (Sec. 3.1): row rho = s*r1 + tau, column kappa = u*g + c,
+  // A'[rho][kappa] = w[u - s][c - tau] when both differences lie in [0, kt).
+  const int g = T.g, mb = T.mb, kp = T.kprime;
+  auto aval = [&](int rho, int kappa) -> float {
+    int s = rho / r1, tau = rho % r1, u = kappa / g, c = kappa % g;
+    int dy = u - s, dx = c - tau;
+    if (dy < 0 || dy >= kt || dx < 0 || dx >= kt) return 0.f;
+    return T.wfused32[dy * kt + dx];
+  };
+  std::vector<char> colnz(kp, 0);
+  for (int kap = 0; kap < kp; kap++)
+    for (int rho = 0; rho < M && !colnz[kap]; rho++)
+      if (aval(rho, kap) != 0.f) colnz[kap] = 1;
+
+  // Structured sparsity conversion (Sec. 3.2).
+  auto pairs = hierarchical_matching(kp, g, kt);
+  std::vector<int> order;
+  for (auto& pr : pairs) {
+    bool a_nz = colnz[pr.first];
+    bool b_nz = pr.second >= 0 && colnz[pr.second];
+    if (pr.second < 0) T.zero_cols++;
+    if (drop_zero_pairs && !a_nz && !b_nz) {
+      T.dropped_pairs++;
+      continue;
+    }
+    order.push_back(pr.first);
+    order.push_back(pr.second);
+  }
+  while (order.size() % Tile2D::KCHUNK) order.push_back(-1);
+  T.order = order;
+  const int kpad = (int)order.size();
+  T.kpad = kpad;
+  const int half = kpad / 2;
+
+  // Weight pieces: w * 2^s = p0 + p1 + p2, each RN-even in the 16-bit word.  FP16 scales
+  // the weights so that the largest is in [0.5, 1) (keeps the pieces out of the subnormal
+  // range); BF16 has FP32's exponent range and uses s = 0.  Three BF16 pieces hold an FP32
+  // weight exactly (3 x 8 significand bits).
+  if (max_pieces < 1 || max_pieces > 3) return "bad piece count";
+  double wmax = 0.0;
+  for (float v : T.wfused32) wmax = std::max(wmax, (double)std::fabs(v));
+  int s = 0;
+  if (word == Word::FP16 && wmax > 0.0) {
+    int e;
+    std::frexp(wmax, &e);  // wmax = f * 2^e, f in [0.5, 1)
+    s = -e;
+  }
+  T.wscale_log2 = s;
+  // Compression with 2:4 metadata (Sec. 3.3, Metadata; Sec. 2.1 for sub-2:4 groups).
+  for (int pc = 0; pc < 3; pc++) T.a_val[pc].assign((size_t)M * half, 0.f);
+  T.a_idx.assign((size_t)M * half, 0);
+  bool piece_used[3] = {false, false, false};
+  for (int rho = 0; rho < M; rho++) {
+    for (int q = 0; q < kpad / 4; q++) {
+      int pos[4], nnz = 0;
+      float val[4];
+      for (int e = 0; e < 4; e++) {
+        int col = order[4 * q + e];
+        float v = col >= 0 ? aval(rho, col) : 0.f;
+        if (v != 0.f) {
+          if (nnz >= 2) return "permuted staircase violates 2:4 (row " + std::to_string(rho) + ")";
+          pos[nnz] = e;
+          val[nnz] = v;
+          nnz++;
+        }
+      }
+      // fill sub-2:4 groups with the lowest unused positions (their values are zero)
+      for (int e = 0; nnz < 2 && e < 4; e++) {
+        bool used = false;
+        for (int j = 0; j < nnz; j++) used |= (pos[j] == e);
+        if (!used) {
+          pos[nnz] = e;
+          val[nnz] = 0.f;
+          nnz++;
+        }
+      }
+      if (pos[0] > pos[1]) {
+        std::swap(pos[0], pos[1]);
+        std::swap(val[0], val[1]);
+      }
+      for (int j = 0; j < 2; j++) {
+        size_t at = (size_t)rho * half + 2 * q + j;
+        float rem = std::ldexp(val[j], s);  // exact (power-of-two scale)
+        for (int pc = 0; pc < max_pieces; pc++) {
+          float hv = half_bits_to_float(to_half_bits(rem, word), word);
+          T.a_val[pc][at] = hv;
+          if (hv != 0.f) piece_used[pc] = true;
+          rem -= hv;  // exact: the residual of a round-to-nearest is representable
+        }
+        T.a_idx[at] = (uint8_t)pos[j];
+      }
+    }
+  }
+  T.a_pieces = 1;
+  for (int pc = 1; pc < max_pieces; pc++)
+    if (piece_used[pc]) T.a_pieces = pc + 1;
+  // TMEM image of A'' (lane = row; column j holds compressed elements 2j (low) and 2j+1).
+  const int pieces = T.a_pieces;
+  const int wcols = kpad / 4;
+  T.a_words.assign((size_t)pieces * M * wcols, 0u);
+  for (int p = 0; p < pieces; p++)
+    for (int rho = 0; rho < M; rho++)
+      for (int j = 0; j < wcols; j++) {
+        const std::vector<float>& src = T.a_val[p];
+        uint32_t lo = to_half_bits(src[(size_t)rho * half + 2 * j], word);
+        uint32_t hi = to_half_bits(src[(size_t)rho * half + 2 * j + 1], word);
+        T.a_words[((size_t)p * M + rho) * wcols + j] = lo | (hi << 16);
+      }
+  // TMEM image of the metadata: one column per 32-wide K chunk.  Row rho's chunk word has
+  // nibble (idx0 | idx1 << 2) for group q at bits 4q.  In each block of 16 lanes, row rr < 8
+  // keeps its groups 0-3 in lane rr bits [0,16) and groups 4-7 in lane rr+8 bits [0,16);
+  // row rr >= 8 keeps groups 0-3 in lane rr-8 bits [16,32) and groups 4-7 in lane rr
+  // bits [16,32).  (Layout measured on sm_103a for kind::f16, M = 128, selector 0.)
+  const int nch = kpad / Tile2D::KCHUNK;
+  T.meta_words.assign((size_t)M * nch, 0u);
+  for (int kc = 0; kc < nch; kc++) {
+    for (int rho = 0; rho < M; rho++) {
+      uint32_t wrow = 0;
+      for (int q = 0; q < 8; q++) {
+        size_t at = (size_t)rho * half + kc * 16 + 2 * q;
+        wrow |= (uint32_t)(T.a_idx[at] | (T.a_idx[at + 1] << 2)) << (4 * q);
+      }
+      uint32_t lo16 = wrow & 0xffffu, hi16 = wrow >> 16;
+      int base = rho & ~15, rr = rho & 15;
+      if (rr < 8) {
+        T.meta_words[(size_t)(base + rr) * nch + kc] |= lo16;
+        T.meta_words[(size_t)(base + rr + 8) * nch + kc] |= hi16;
+      } else {
+        T.meta_words[(size_t)(base + rr - 8) * nch + kc] |= lo16 << 16;
+        T.meta_words[(size_t)(base + rr) * nch + kc] |= hi16 << 16;
+      }
+    }
+  }
+  // Lookup table (Sec. 3.3): tile-word offset of each permuted K row relative to the patch's
+  // base (py*R2*P + px*R1).  The tile starts G cells before the tile's first output, the
+  // patch window R cells before the patch's first output.  A zero column reads its pair
+  // partner (any finite value works: its weights are zero).
+  T.lut.assign(kpad, 0);
+  auto off = [&](int col) { return (col / g + geo.G - R) * geo.P + (col % g + geo.G - R); };
+  for (int kap = 0; kap < kpad; kap++) {
+    int col = order[kap];
+    if (col < 0) col = order[kap ^ 1];
+    T.lut[kap] = col >= 0 ? off(col) : 0;
+  }
+  (void)mb;
+  return "";
+}
+
+// ---------------------------------------------------------------------------------------
+// Cost model of Sec. 3.3: T = max(T_compute, T_memory), with
+//   T_compute = N_MMA * CPI / (f N_tcu)  (here: executed sparse MMA flops / tensor rate),
+//   T_memory  = max((data_R + data_W) / bw_G, (data_transW + data_transR) / bw_S),
+//   data_transR = data_transW = k' (m'/2 + n') elements (reading: m means m').
+// ---------------------------------------------------------------------------------------
+double layout_cost_seconds(int kt, int r1, int r2, int64_t H, int64_t W, int kpad, double tensor_flops,
+                           double hbm_bytes_per_s, double smem_bytes_per_s) {
+  const double mprime = (double)r1 * r2;
+  const double kprime = (double)(kt + r1 - 1) * (kt + r2 - 1);
+  const double nprime = (double)H * (double)W / mprime;
+  const double n_mma = std::ceil(mprime / 128.0) * std::ceil((double)kpad / 32.0) * std::ceil(nprime / 128.0);
+  const double t_compute = n_mma * 2.0 * 128.0 * 128.0 * 32.0 / tensor_flops;
+  const double data_rw = 8.0 * (double)H * (double)W;
+  const double trans = kprime * (mprime / 2.0 + nprime) * 2.0;
+  const double t_memory = std::max(data_rw / hbm_bytes_per_s, 2.0 * trans / smem_bytes_per_s);
+  return std::max(t_compute, t_memory);
+}
+
+}  // namespace spst

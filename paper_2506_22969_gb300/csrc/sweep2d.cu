@@ -1,0 +1,447 @@
+// Sparse tensor-core stencil sweep for 2D grids on sm_103a (GB300).
+//
+// One launch = one sweep of t fused time steps over the whole grid.  The method is the
+// matrix form of Sec. 3: every r2 x r1 output patch is one column of D = A'' B'', where A''
+// is the crushed staircase (Sec. 3.1) after the 2:4 permutation (Sec. 3.2) and B'' holds
+// the patch's deduplicated input window in the permuted K order.  The kernel follows the
+// three-stage template of Sec. 3.3 (load -> sparse MMA -> write back, double-buffered),
+// re-planned for Blackwell:
+//   * warp 0 streams 128 x 128-output halo tiles from the padded input grid with TMA
+//     (cp.async.bulk.tensor.2d) into a 2-stage ring;
+//   * warps 8-15 build B'' one 32-row K chunk at a time from the tile through the lookup
+//     table (Sec. 3.3), subtract a per-patch reference value (so the tensor cores see
+//     deviations, see below), convert to FP16/BF16 (split: hi and lo words) and store
+//     into a 3-slot ring in the UMMA K-major layout;
+//   * warp 1 issues tcgen05.mma.sp (kind::f16, M = 128, N = 128, K = 32) with A'' and its
+//     2:4 metadata resident in TMEM, accumulating in FP32 in one of one or two TMEM
+//     accumulators.  The weights are held as an exact sum of up to three 16-bit pieces and
+//     the data as one word (single) or hi + lo (split); each K chunk issues the term table
+//     A_i B_j given by the host (single: A_0 B_0 + A_1 B_0; split: A_0 B_0 + A_0 B_1 + A_1 B_0
+//     + A_2 B_0), so weight rounding never enters the result as a systematic error;
+//   * warps 4-7 drain the accumulator with tcgen05.ld, add back reference * sum(weights)
+//     and store coalesced rows (plus periodic ghost images when writing a padded grid).
+// Per-patch reference: out = c * S + sum_kappa A''[rho,kappa] (B''[kappa,n] - c) equals the
+// stencil exactly for any c; with c = the patch's own input value the operands are small
+// deviations, so operand rounding and accumulation errors do not bias the mean field.
+// Every mbarrier wait is bounded by %globaltimer; a timeout records SPST_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace spst {
+
+namespace {
+
+constexpr int kStatusTimeout = 5;
+// Bound of the waits that drain a CTA's own copies and MMAs before it exits (independent of
+// the caller's wait limit, so that a short limit never lets a CTA leave with work in flight).
+constexpr uint64_t kDrainNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded single-thread wait: returns false on timeout, or when abort_flag (may be null) is
+// set by another role.  A timeout sets abort_flag and records SPST_ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns, volatile int* abort_flag,
+                                          int* status) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (abort_flag && *abort_flag) return false;
+    if (gtimer() - t0 > limit_ns) {
+      if (abort_flag) *abort_flag = 1;
+      atomicCAS(status, 0, kStatusTimeout);
+      return false;
+    }
+  }
+}
+
+// Warp-uniform bounded wait: every lane polls the barrier (so each lane acquires the phase);
+// the give-up decision is lane 0's and is taken by the whole warp.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns, volatile int* abort_flag,
+                                          int* status) {
+  const uint64_t t0 = gtimer();
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    const bool d = mbar_try(bar, parity);
+    if (__all_sync(0xffffffffu, d)) return true;
+    int give_up = 0;
+    if (lane == 0) give_up = (*abort_flag) ? 1 : ((gtimer() - t0 > limit_ns) ? 2 : 0);
+    give_up = __shfl_sync(0xffffffffu, give_up, 0);
+    if (give_up) {
+      if (lane == 0 && give_up == 2) {
+        *abort_flag = 1;
+        atomicCAS(status, 0, kStatusTimeout);
+      }
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; no swizzle, base offset 0
+  return d;
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi, int fp16) {
+  uint32_t r;
+  if (fp16)
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  else
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__device__ __forceinline__ void unpack2(uint32_t v, int fp16, float& lo, float& hi) {
+  if (fp16) {
+    unsigned short a = (unsigned short)(v & 0xffffu), b = (unsigned short)(v >> 16);
+    asm("cvt.f32.f16 %0, %1;" : "=f"(lo) : "h"(a));
+    asm("cvt.f32.f16 %0, %1;" : "=f"(hi) : "h"(b));
+  } else {
+    lo = __uint_as_float(v << 16);
+    hi = __uint_as_float(v & 0xffff0000u);
+  }
+}
+
+struct SmemLayout {
+  uint32_t halo_stride, off_b, slot_bytes, off_lut, off_cv, off_bar, total;
+  __host__ __device__ explicit SmemLayout(const Sweep2DParams& p) {
+    uint32_t halo = (uint32_t)p.box_h * (uint32_t)p.P * 4u;
+    halo_stride = (halo + 1023u) & ~1023u;
+    off_b = halo_stride * kHaloStages;
+    slot_bytes = (uint32_t)p.b_pieces * (uint32_t)kPieceBytes;
+    off_lut = off_b + slot_bytes * kBSlots;
+    off_cv = off_lut + (((uint32_t)p.kpad * 4u + 15u) & ~15u);
+    off_bar = off_cv + 2u * 128u * 4u;
+    total = off_bar + 256u;
+  }
+};
+
+// barrier indices (8 bytes each, from off_bar)
+constexpr int BAR_HFULL = 0, BAR_HEMPTY = 2, BAR_BFULL = 4, BAR_BEMPTY = 7, BAR_AFULL = 10, BAR_AEMPTY = 12,
+              BAR_CVFULL = 14, BAR_FINAL = 16;
+constexpr int BAR_COUNT = 17;  // 136 bytes, below the TMEM slot at +192
+constexpr uint32_t TMEM_COLS = 512;
+
+__global__ void __launch_bounds__(kSweepThreads, 1)
+    sweep2d_kernel(const __grid_constant__ CUtensorMap tmap_in, const Sweep2DParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (sbase - raw);
+  const SmemLayout L(p);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar0 = sbase + L.off_bar;
+  auto bar = [&](int i) -> uint32_t { return bar0 + 8u * (uint32_t)i; };
+  uint32_t* tmem_slot = (uint32_t*)(smem + L.off_bar + 192);               // 16-byte aligned
+  volatile int* abort_flag = (volatile int*)(smem + L.off_bar + 208);
+  int32_t* lut_s = (int32_t*)(smem + L.off_lut);
+  float* cvals = (float*)(smem + L.off_cv);
+  const int pieces = p.a_pieces;
+  const int acols = p.kpad / 4;
+  const int nacc = p.nacc;
+  const uint64_t wait_ns = p.wait_ns;
+
+  // ---------------- set-up ----------------
+  if (threadIdx.x == 0) {
+    mbar_init(bar(BAR_HFULL + 0), 1);
+    mbar_init(bar(BAR_HFULL + 1), 1);
+    mbar_init(bar(BAR_HEMPTY + 0), 8);
+    mbar_init(bar(BAR_HEMPTY + 1), 8);
+    for (int s = 0; s < kBSlots; s++) {
+      mbar_init(bar(BAR_BFULL + s), 8);
+      mbar_init(bar(BAR_BEMPTY + s), 1);
+    }
+    for (int a = 0; a < 2; a++) {
+      mbar_init(bar(BAR_AFULL + a), 1);
+      mbar_init(bar(BAR_AEMPTY + a), 4);
+      mbar_init(bar(BAR_CVFULL + a), 8);
+    }
+    mbar_init(bar(BAR_FINAL), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  for (int i = threadIdx.x; i < p.kpad; i += blockDim.x) lut_s[i] = p.lut[i];
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a_col = 128u * (uint32_t)nacc;  // accumulators first, then A'' pieces, then metadata
+  const uint32_t meta_col = a_col + (uint32_t)(pieces * acols);
+
+  if (warp >= 4 && warp < 8) {
+    // A'' pieces and the metadata into TMEM (lane = output row of the patch).
+    const int q = warp - 4;
+    const int row = 32 * q + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+    for (int pc = 0; pc < pieces; pc++) {
+      const uint32_t* src = p.a_words + ((size_t)pc * 128 + row) * acols;
+      for (int c = 0; c < acols; c += 8) {
+        uint32_t v0 = src[c], v1 = src[c + 1], v2 = src[c + 2], v3 = src[c + 3];
+        uint32_t v4 = src[c + 4], v5 = src[c + 5], v6 = src[c + 6], v7 = src[c + 7];
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                         lane_addr + a_col + (uint32_t)(pc * acols + c)),
+                     "r"(v0), "r"(v1), "r"(v2), "r"(v3), "r"(v4), "r"(v5), "r"(v6), "r"(v7));
+      }
+    }
+    // chunk c's metadata column: an 8-column-aligned pair per two chunks, the instruction's
+    // sparsity selector (0/1) picks the column inside the pair
+    for (int c = 0; c < p.kchunks; c++) {
+      uint32_t v = p.meta_words[(size_t)row * p.kchunks + c];
+      asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(
+                       lane_addr + meta_col + 8u * (uint32_t)(c >> 1) + (uint32_t)(c & 1)),
+                   "r"(v));
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+
+  const int ntiles_cta = (p.num_tiles > (int)blockIdx.x) ? (p.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      const uint32_t bytes = (uint32_t)p.box_h * (uint32_t)p.P * 4u;
+      int issued = 0;
+      for (int li = 0; li < ntiles_cta; li++) {
+        const int stage = li & 1;
+        if (li >= 2 && !mbar_wait(bar(BAR_HEMPTY + stage), ((li >> 1) - 1) & 1, wait_ns, abort_flag, p.status)) break;
+        const int tt = (int)blockIdx.x + li * (int)gridDim.x;
+        const int x0 = (tt % p.tiles_x) * 128, y0 = (tt / p.tiles_x) * 128;
+        const uint32_t dst = sbase + (uint32_t)stage * L.halo_stride;
+        mbar_expect_tx(bar(BAR_HFULL + stage), bytes);
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                dst),
+            "l"(&tmap_in), "r"(x0), "r"(y0), "r"(bar(BAR_HFULL + stage))
+            : "memory");
+        issued++;
+      }
+      // the CTA never exits with one of its copies in flight (at most the last two can be)
+      for (int li = (issued > 2 ? issued - 2 : 0); li < issued; li++)
+        mbar_wait(bar(BAR_HFULL + (li & 1)), (li >> 1) & 1, kDrainNs, nullptr, p.status);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t idesc = 0;
+      idesc |= 1u << 2;                      // sparse
+      idesc |= 1u << 4;                      // D = FP32
+      idesc |= (p.fp16 ? 0u : 1u) << 7;      // A: FP16 (0) / BF16 (1)
+      idesc |= (p.fp16 ? 0u : 1u) << 10;     // B: FP16 (0) / BF16 (1)
+      idesc |= (uint32_t)(128 >> 3) << 17;   // N = 128
+      idesc |= (uint32_t)(128 >> 4) << 24;   // M = 128
+      uint32_t gchunk = 0;
+      bool ok = true;
+      for (int li = 0; li < ntiles_cta && ok; li++) {
+        const int acc = li % nacc, use = li / nacc;
+        if (use > 0 && !mbar_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t dcol = tmem + (uint32_t)(acc * 128);
+        for (int kc = 0; kc < p.kchunks; kc++, gchunk++) {
+          const uint32_t slot = gchunk % kBSlots, su = gchunk / kBSlots;
+          if (!mbar_wait(bar(BAR_BFULL + slot), su & 1, wait_ns, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t bslot = sbase + L.off_b + slot * L.slot_bytes;
+          const uint32_t meta = tmem + meta_col + 8u * (uint32_t)(kc >> 1);
+          const uint32_t idesc_kc = idesc | (uint32_t)(kc & 1);  // sparsity selector
+          for (int term = 0; term < p.nterms; term++) {
+            const uint32_t a_addr = tmem + a_col + (uint32_t)(p.term_a[term] * acols + kc * 8);
+            const uint64_t bdesc = make_sdesc(bslot + (uint32_t)(p.term_b[term] * kPieceBytes), kLBO, kSBO);
+            const uint32_t en = (kc > 0 || term > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n"
+                " tcgen05.mma.sp.cta_group::1.kind::f16 [%0], [%1], %2, [%3], %4, q;\n}" ::"r"(dcol),
+                "r"(a_addr), "l"(bdesc), "r"(meta), "r"(idesc_kc), "r"(en));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              bar(BAR_BEMPTY + slot)));
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            bar(BAR_AFULL + acc)));
+      }
+      // every MMA issued above completes before TMEM is released
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(BAR_FINAL)));
+      mbar_wait(bar(BAR_FINAL), 0, kDrainNs, nullptr, p.status);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- epilogue ----------------
+    const int q = warp - 4;
+    const int rho = 32 * q + lane;
+    const int ry = rho >> 4, rx = rho & 15;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+    for (int li = 0; li < ntiles_cta; li++) {
+      const int acc = li % nacc, use = li / nacc;
+      if (!warp_wait(bar(BAR_AFULL + acc), use & 1, wait_ns, abort_flag, p.status)) break;
+      if (!warp_wait(bar(BAR_CVFULL + acc), use & 1, wait_ns, abort_flag, p.status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int tt = (int)blockIdx.x + li * (int)gridDim.x;
+      const int x0 = (tt % p.tiles_x) * 128, y0 = (tt / p.tiles_x) * 128;
+      const float* cv = cvals + acc * 128;
+      for (int cg = 0; cg < 8; cg++) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(lane_addr + (uint32_t)(acc * 128 + cg * 16)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const int n = cg * 16 + j;
+          const int px = (n >> 3) & 7, py = ((n >> 6) << 3) + (n & 7);
+          const int y = y0 + py * 8 + ry, x = x0 + px * 16 + rx;
+          const float c = cv[n];
+          const float val = fmaf(c, p.S_lo, fmaf(c, p.S_hi, __uint_as_float(v[j]) * p.wscale));
+          if (y < p.H && x < p.W) {
+            const int G = p.out_off;
+            p.out[(int64_t)(y + G) * p.out_pitch + (x + G)] = val;
+            if (p.out_ghost) {
+              const int ys[2] = {y < G ? y + p.H + G : -1, y >= p.H - G ? y - p.H + G : -1};
+              const int xs[2] = {x < G ? x + p.W + G : -1, x >= p.W - G ? x - p.W + G : -1};
+              for (int a = 0; a < 2; a++)
+                if (ys[a] >= 0) p.out[(int64_t)ys[a] * p.out_pitch + (x + G)] = val;
+              for (int b = 0; b < 2; b++)
+                if (xs[b] >= 0) p.out[(int64_t)(y + G) * p.out_pitch + xs[b]] = val;
+              for (int a = 0; a < 2; a++)
+                for (int b = 0; b < 2; b++)
+                  if (ys[a] >= 0 && xs[b] >= 0) p.out[(int64_t)ys[a] * p.out_pitch + xs[b]] = val;
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(BAR_AEMPTY + acc));
+    }
+  } else if (warp >= 8) {
+    // ---------------- B'' gather ----------------
+    const int gw = warp - 8;
+    const int h = lane >> 4, pl = lane & 15;
+    const uint32_t pairoff = (uint32_t)((pl >> 2) * kLBO + (pl & 3) * 4);
+    const int P = p.P, G = p.G;
+    uint32_t gchunk = 0;
+    int base_i[8], n_i[8];
+    uint32_t soff_i[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const int pp = gw + 8 * i;
+      const int n = (pp >> 3) * 16 + (pp & 7) + 8 * h;
+      const int px = (n >> 3) & 7, py = ((n >> 6) << 3) + (n & 7);
+      n_i[i] = n;
+      base_i[i] = py * 8 * P + px * 16;
+      soff_i[i] = (uint32_t)((n >> 3) * kSBO + (n & 7) * 16) + pairoff;
+    }
+    for (int li = 0; li < ntiles_cta; li++) {
+      const int stage = li & 1, acc = li % nacc, use = li / nacc;
+      if (!warp_wait(bar(BAR_HFULL + stage), (li >> 1) & 1, wait_ns, abort_flag, p.status)) break;
+      const float* tile = (const float*)(smem + (size_t)stage * L.halo_stride);
+      float c_i[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) c_i[i] = tile[base_i[i] + G * P + G];
+      if (use > 0 && !warp_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
+      if (pl == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) cvals[acc * 128 + n_i[i]] = c_i[i];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(BAR_CVFULL + acc));
+      bool ok = true;
+      for (int kc = 0; kc < p.kchunks; kc++, gchunk++) {
+        const uint32_t slot = gchunk % kBSlots, su = gchunk / kBSlots;
+        if (su > 0 && !warp_wait(bar(BAR_BEMPTY + slot), (su - 1) & 1, wait_ns, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        const int la = lut_s[kc * 32 + 2 * pl], lb = lut_s[kc * 32 + 2 * pl + 1];
+        uint8_t* bs = smem + L.off_b + slot * L.slot_bytes;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const float da = tile[base_i[i] + la] - c_i[i];
+          const float db = tile[base_i[i] + lb] - c_i[i];
+          const uint32_t hi = pack2(da, db, p.fp16);
+          *(uint32_t*)(bs + soff_i[i]) = hi;
+          if (p.b_pieces > 1) {
+            float ha, hb;
+            unpack2(hi, p.fp16, ha, hb);
+            *(uint32_t*)(bs + kPieceBytes + soff_i[i]) = pack2(da - ha, db - hb, p.fp16);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(BAR_BFULL + slot));
+      }
+      if (!ok) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(BAR_HEMPTY + stage));
+    }
+  }
+
+  // ---------------- teardown ----------------
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+}  // namespace
+
+size_t sweep2d_smem_bytes(const Sweep2DParams& p) { return (size_t)SmemLayout(p).total + 1024; }
+
+cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p, int num_sms, cudaStream_t stream) {
+  const size_t smem = sweep2d_smem_bytes(p);
+  cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
+  if (grid < 1) return cudaSuccess;
+  sweep2d_kernel<<<grid, kSweepThreads, smem, stream>>>(tmap_in, p);
+  return cudaGetLastError();
+}
+
+}  // namespace spst

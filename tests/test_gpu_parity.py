@@ -1,0 +1,174 @@
+"""GPU parity: the sparse tensor-core path (through the C ABI) against the FP64 oracle.
+
+Tolerances (rel-L2 over the whole grid, FP64, after the full run): single-word operands
+(FP16/BF16) 2e-3, split hi+lo operands 1e-5; the plain FP32 CUDA-core comparator 1e-5.
+"""
+import numpy as np
+import pytest
+
+from paper_2506_22969_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp16": 2e-3, "bf16": 2e-3, "fp16_split": 1e-5, "bf16_split": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_22969_gb300 import build
+    build.build()
+    binding.load()
+    return torch
+
+
+def _run_sparse(torch, u, w, steps, dtype, bc, t, shape):
+    plan = binding.Plan(w, u.shape, dtype=dtype, bc=bc, fusion_depth=t, shape=shape)
+    x = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).cuda()
+    y = torch.empty_like(x)
+    plan.run(x, y, steps)
+    assert binding.device_status() == 0
+    return y.cpu().numpy().astype(np.float64), plan
+
+
+CASES = [
+    # (shape, r, recipe, dims, steps, bc, dtype, t)
+    ("star", 1, "heat", (512, 512), 8, "dirichlet", "fp16", 1),
+    ("star", 1, "heat", (512, 512), 8, "dirichlet", "bf16_split", 1),
+    ("box", 1, "random", (300, 260), 20, "periodic", "bf16", 1),
+    ("box", 1, "random", (300, 260), 20, "periodic", "bf16_split", 1),
+    ("box", 1, "random", (256, 384), 10, "periodic", "fp16_split", 1),
+    ("box", 1, "random", (130, 200), 7, "dirichlet", "bf16", 1),
+    ("box", 1, "random", (384, 320), 10, "periodic", "bf16_split", 3),
+    ("box", 1, "random", (256, 256), 11, "periodic", "bf16", 2),
+    ("star", 3, "gaussian", (260, 300), 6, "periodic", "bf16_split", 1),
+    ("box", 3, "gaussian", (260, 300), 6, "periodic", "bf16", 1),
+    ("box", 3, "gaussian", (200, 256), 5, "dirichlet", "fp16_split", 1),
+    ("box", 2, "random", (128, 128), 4, "periodic", "bf16_split", 1),
+]
+
+
+@pytest.mark.parametrize("shape,r,recipe,dims,steps,bc,dtype,t", CASES)
+def test_sparse_matches_oracle(torch_cuda, oracle_mod, shape, r, recipe, dims, steps, bc, dtype, t):
+    w = inputs.stencil_weights(shape, 2, r, recipe, seed=11)
+    u = inputs.uniform01(5, dims)
+    ref = oracle_mod.run(u, w, bc, steps)
+    got, _ = _run_sparse(torch_cuda, u, w, steps, dtype, bc, t, shape)
+    l2, linf = oracle_mod.rel_errors(got, ref)
+    assert np.all(np.isfinite(got))
+    assert l2 <= TOL[dtype], (l2, linf)
+
+
+def test_zero_and_one_step(torch_cuda, oracle_mod):
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=3)
+    u = inputs.uniform01(6, (200, 136))
+    got0, _ = _run_sparse(torch_cuda, u, w, 0, "bf16", "periodic", 1, "box")
+    np.testing.assert_array_equal(got0, u.astype(np.float64))
+    got1, _ = _run_sparse(torch_cuda, u, w, 1, "bf16_split", "periodic", 1, "box")
+    assert oracle_mod.rel_errors(got1, oracle_mod.run(u, w, "periodic", 1))[0] <= 1e-5
+
+
+def test_closed_form_fourier_mode(torch_cuda):
+    """Periodic closed form, no oracle: u0 = 1/2 + 1/2 cos(theta.x) evolves to
+    1/2 S^T + 1/2 Re(lambda^T e^{i theta.x}), S = sum w, lambda = sum_o w[o] e^{i theta.o};
+    100 steps on the split path."""
+    H, W = 256, 384
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=8)
+    w64 = w.astype(np.float64)
+    th = np.array([2 * np.pi * 3 / H, 2 * np.pi * 5 / W])
+    y, x = np.mgrid[0:H, 0:W]
+    phase = th[0] * y + th[1] * x
+    lam = sum(w64[a + 1, b + 1] * np.exp(1j * (th[0] * a + th[1] * b)) for a in (-1, 0, 1) for b in (-1, 0, 1))
+    S = float(np.sum(w64))
+    T = 100
+    u0 = 0.5 + 0.5 * np.cos(phase)
+    ref = 0.5 * S ** T + 0.5 * np.real(lam ** T * np.exp(1j * phase))
+    got, _ = _run_sparse(torch_cuda, u0, w, T, "bf16_split", "periodic", 1, "box")
+    err = np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2))
+    assert err <= 1e-5, err
+
+
+def test_direct_fp32_matches_oracle(torch_cuda, oracle_mod):
+    torch = torch_cuda
+    for shape, r, recipe, bc in [("box", 1, "random", "periodic"), ("star", 3, "gaussian", "dirichlet"),
+                                 ("box", 3, "gaussian", "periodic")]:
+        w = inputs.stencil_weights(shape, 2, r, recipe, seed=4)
+        u = inputs.uniform01(7, (130, 200))
+        x = torch.from_numpy(u).cuda()
+        out = torch.empty_like(x)
+        work = torch.empty_like(x)
+        binding.direct_run(w, x, out, work, 9, bc=bc)
+        ref = oracle_mod.run(u, w, bc, 9)
+        assert oracle_mod.rel_errors(out.cpu().numpy(), ref)[0] <= 1e-6
+
+
+def test_direct_fp32_3d(torch_cuda, oracle_mod):
+    torch = torch_cuda
+    w = inputs.stencil_weights("box", 3, 1, "random", seed=5)
+    u = inputs.uniform_pm1(3, (20, 24, 40))
+    x = torch.from_numpy(u).cuda()
+    out, work = torch.empty_like(x), torch.empty_like(x)
+    binding.direct_run(w, x, out, work, 5, bc="dirichlet")
+    ref = oracle_mod.run(u, w, "dirichlet", 5)
+    assert oracle_mod.rel_errors(out.cpu().numpy(), ref)[0] <= 1e-6
+
+
+def test_error_norms_kernel(torch_cuda):
+    torch = torch_cuda
+    a = inputs.uniform01(1, (1000, 37))
+    b = inputs.uniform01(2, (1000, 37))
+    l2, linf, raw = binding.error_norms(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+    d = a.astype(np.float64) - b.astype(np.float64)
+    assert abs(raw[0] - np.sum(d * d)) <= 1e-9 * np.sum(d * d)
+    assert raw[2] == np.max(np.abs(d)) and raw[3] == np.max(np.abs(b.astype(np.float64)))
+
+
+def test_run_host_equals_run(torch_cuda):
+    torch = torch_cuda
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=3)
+    u = inputs.uniform01(6, (256, 256))
+    plan = binding.Plan(w, u.shape, dtype="bf16_split", bc="periodic")
+    x = torch.from_numpy(u).cuda()
+    y = torch.empty_like(x)
+    plan.run(x, y, 12)
+    host_out = torch.empty((256, 256), dtype=torch.float32).pin_memory()
+    plan.run_host(torch.from_numpy(u).pin_memory(), host_out, 12)
+    np.testing.assert_array_equal(host_out.numpy(), y.cpu().numpy())
+
+
+def test_full_size_box9_sampled(torch_cuda, oracle_mod):
+    """Box-2D9P 4096^2, periodic, 100 steps (the benchmark workload): sampled points against
+    the dependence-cone oracle, both precisions, in the launch configuration the bench times."""
+    cfg = inputs.CONFIGS["box2d9p_4096"]
+    w = inputs.stencil_weights(cfg["shape"], 2, cfg["radius"], cfg["recipe"], seed=cfg["seed"])
+    u = inputs.make_grid(cfg["grid"], cfg["seed"], cfg["dims"])
+    rng = np.random.default_rng(0)
+    pts = [tuple(int(v) for v in rng.integers(0, 4096, 2)) for _ in range(24)] + [(0, 0), (4095, 4095), (0, 4095)]
+    ref = np.array([oracle_mod.point(u, w, "periodic", cfg["steps"], p) for p in pts])
+    for dtype, tol in (("bf16", 2e-3), ("bf16_split", 1e-5)):
+        got, _ = _run_sparse(torch_cuda, u, w, cfg["steps"], dtype, "periodic", 1, "box")
+        vals = np.array([got[p] for p in pts])
+        rel = np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2))
+        assert rel <= tol, (dtype, rel)
+
+
+def test_bounded_wait_reports_timeout(torch_cuda):
+    """A wait limit far below a tile's load time makes every CTA's first wait run out: the
+    kernel drains its own copies, frees TMEM, returns, and the host reads SPST_ERR_TIMEOUT;
+    the context stays usable."""
+    torch = torch_cuda
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=3)
+    u = inputs.uniform01(6, (512, 512))
+    plan = binding.Plan(w, u.shape, dtype="bf16", bc="periodic")
+    x = torch.from_numpy(u).cuda()
+    y = torch.empty_like(x)
+    binding.set_wait_limit_ns(1)
+    try:
+        plan.run(x, y, 2)
+        assert binding.device_status() == 5
+    finally:
+        binding.set_wait_limit_ns(0)
+    plan.run(x, y, 2)
+    assert binding.device_status() == 0

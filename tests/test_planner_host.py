@@ -1,0 +1,215 @@
+"""Host-only checks of the C-ABI library: it loads, exports every declared symbol, and its
+planner tables are bit-exact against the oracle's literal restatement of Sec. 3.1-3.3.
+
+No GPU is needed: sparstencil_plan and sparstencil_plan_tables are host-only calls.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import morph
+from oracle.morph import ZERO
+from paper_2506_22969_gb300 import binding, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_22969_gb300 import build
+    build.build()
+    return binding.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    with open(os.path.join(ROOT, "include", "sparstencil.h")) as f:
+        text = f.read()
+    declared = set(re.findall(r"\b(sparstencil_[a-z_]+)\s*\(", text))
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(binding.EXPORTS) <= declared
+
+
+def _bf16(x):
+    import torch
+    return torch.tensor(np.asarray(x, np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def _fp16(x):
+    return np.asarray(x, np.float32).astype(np.float16).astype(np.float32)
+
+
+def _oracle_order(wf, k, r1, r2, drop=True):
+    """Algorithm 1 order, dropping pairs whose two A' columns are all zero, padded to 32."""
+    A = morph.crushed_weights(wf, r1, r2)
+    g, mb = k + r1 - 1, k + r2 - 1
+    nz = np.any(A != 0, axis=0)
+    _, _, M = morph.hierarchical_matching(g * mb, g, k)
+    order = []
+    for a, b in M:
+        if drop and not nz[a] and (b == ZERO or not nz[b]):
+            continue
+        order.extend([a, b])
+    while len(order) % 32:
+        order.append(ZERO)
+    return A, np.array(order)
+
+
+def _composed(w, t):
+    """t-step kernel read off the oracle: one impulse, t steps, correlation orientation."""
+    import oracle
+    r = (w.shape[0] - 1) // 2
+    R = t * r
+    n = 4 * R + 3
+    u = np.zeros((n, n))
+    c = n // 2
+    u[c, c] = 1.0
+    out = oracle.run(u, w.astype(np.float64), "periodic", t)
+    return out[c - R:c + R + 1, c - R:c + R + 1][::-1, ::-1]
+
+
+CASES = [("star", 1, "heat", 1, "bf16"), ("box", 1, "random", 1, "bf16_split"), ("box", 1, "random", 2, "bf16"),
+         ("box", 1, "random", 3, "fp16_split"), ("star", 3, "gaussian", 1, "bf16_split"),
+         ("box", 3, "gaussian", 1, "fp16"), ("box", 2, "random", 1, "bf16")]
+
+
+@pytest.mark.parametrize("shape,r,recipe,t,dtype", CASES)
+def test_planner_tables_against_oracle(lib, oracle_mod, shape, r, recipe, t, dtype):
+    w = inputs.stencil_weights(shape, 2, r, recipe, seed=7)
+    plan = binding.Plan(w, (300, 260), dtype=dtype, bc="periodic", fusion_depth=t, shape=shape)
+    info = plan.info()
+    tb = plan.tables()
+    k = 2 * t * r + 1
+    # composed weights equal the oracle's t-step impulse response
+    np.testing.assert_allclose(tb["fused_w"], _composed(w, t), rtol=1e-13, atol=1e-16)
+    wf32 = tb["fused_w"].astype(np.float32).astype(np.float64)
+    A, order = _oracle_order(wf32, k, 16, 8)
+    assert info.r1 == 16 and info.r2 == 8 and info.kprime == A.shape[1]
+    np.testing.assert_array_equal(tb["order"], order)
+    assert info.kpad == len(order) and info.kpad % 32 == 0
+    # decompress and check 2:4, values and un-permutation to A'
+    split = dtype.endswith("split")
+    fp16 = dtype.startswith("fp16")
+    rnd = _fp16 if fp16 else _bf16
+    s = -int(np.frexp(np.max(np.abs(wf32)))[1]) if fp16 else 0  # FP16 pieces hold w * 2^s
+    sc = 2.0 ** s
+    dense_hi = morph.decompress_2_4(tb["a_hi"].astype(np.float64), tb["a_idx"])
+    dense_lo = morph.decompress_2_4(tb["a_lo"].astype(np.float64), tb["a_idx"])
+    assert morph.satisfies_2_4(dense_hi) and morph.satisfies_2_4(dense_hi + dense_lo)
+    Ap = morph.apply_permutation(A, list(order))
+    np.testing.assert_array_equal(dense_hi, rnd(Ap * sc) / sc)
+    if split and not fp16:
+        # three BF16 pieces hold every FP32 weight exactly
+        np.testing.assert_array_equal(dense_hi + dense_lo, Ap)
+    elif split:
+        # FP16's third piece is limited by the subnormal step 2^-24 of the scaled weights
+        assert np.max(np.abs(dense_hi + dense_lo - Ap)) <= 2.0 ** -24 * np.max(np.abs(wf32))
+    else:
+        np.testing.assert_array_equal(dense_lo, rnd((Ap * sc).astype(np.float32) - (dense_hi * sc).astype(np.float32)) / sc)
+    # metadata positions: distinct and ascending inside each group
+    idx = tb["a_idx"].reshape(128, -1, 2)
+    assert np.all(idx[:, :, 0] < idx[:, :, 1])
+
+
+def _emulate_sweep(plan, tb, u, bc, dense):
+    """Host emulation of one sweep through the planner's LUT: padded grid -> halo tiles ->
+    B'' gathered by LUT -> dense A'' @ B'' -> outputs by the patch map."""
+    info = plan.info()
+    H, W = u.shape
+    G, P, bh = info.ghost, info.tile_pitch, info.tile_rows
+    Wp = (W + 2 * G + 3) // 4 * 4
+    up = np.zeros((H + 2 * G, Wp))
+    yy, xx = np.mgrid[-G:H + G, -G:W + G]
+    if bc == "periodic":
+        up[:, :W + 2 * G] = u[yy % H, xx % W]
+    else:
+        inside = (yy >= 0) & (yy < H) & (xx >= 0) & (xx < W)
+        up[:, :W + 2 * G] = np.where(inside, u[np.clip(yy, 0, H - 1), np.clip(xx, 0, W - 1)], 0.0)
+    out = np.full((H, W), np.nan)
+    lut = tb["lut"]
+    for ty in range((H + 127) // 128):
+        for tx in range((W + 127) // 128):
+            tile = np.zeros((bh, P))
+            blk = up[ty * 128:ty * 128 + bh, tx * 128:tx * 128 + P]
+            tile[:blk.shape[0], :blk.shape[1]] = blk
+            flat = tile.ravel()
+            for n in range(128):
+                px, py = (n >> 3) & 7, ((n >> 6) << 3) + (n & 7)
+                base = py * 8 * P + px * 16
+                col = dense @ flat[base + lut]
+                for rho in range(128):
+                    y, x = ty * 128 + py * 8 + rho // 16, tx * 128 + px * 16 + rho % 16
+                    if y < H and x < W:
+                        out[y, x] = col[rho]
+    return out
+
+
+@pytest.mark.parametrize("bc,shape,r,t", [("periodic", "box", 1, 1), ("dirichlet", "star", 1, 1),
+                                          ("periodic", "box", 1, 2), ("periodic", "star", 3, 1)])
+def test_lut_emulation_reproduces_oracle_step(lib, oracle_mod, bc, shape, r, t):
+    """Bit-level check of every table the kernel consumes: with exact dyadic weights the
+    emulated sweep (LUT gather, permuted A'', patch map) equals t oracle steps exactly."""
+    side = 2 * r + 1
+    mask = inputs.stencil_mask(shape, 2, r)
+    w = np.where(mask, np.arange(1, side * side + 1).reshape(side, side) / 256.0, 0.0).astype(np.float32)
+    u = np.random.default_rng(3).integers(-8, 9, size=(140, 200)).astype(np.float64) / 8.0
+    plan = binding.Plan(w, u.shape, dtype="bf16", bc=bc, fusion_depth=t, shape=shape)
+    tb = plan.tables()
+    dense = morph.decompress_2_4(tb["a_hi"].astype(np.float64) + tb["a_lo"], tb["a_idx"])
+    ref = oracle_mod.run(u, w.astype(np.float64), bc, t)
+    if t == 1:
+        got = _emulate_sweep(plan, tb, u, bc, dense)
+        np.testing.assert_array_equal(got, ref)
+    else:
+        # fused weights are not exact in BF16: compare with the oracle at the weight rounding level
+        dense64 = morph.apply_permutation(morph.crushed_weights(tb["fused_w"], 16, 8), list(tb["order"]))
+        got = _emulate_sweep(plan, tb, u, bc, dense64)
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+
+
+def test_remainder_tables(lib):
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
+    plan = binding.Plan(w, (512, 512), dtype="bf16", bc="periodic", fusion_depth=3)
+    t3 = plan.tables(0)
+    t1 = plan.tables(1, remainder_depth=1)
+    t2 = plan.tables(1, remainder_depth=2)
+    assert t3["fused_w"].shape == (7, 7) and t2["fused_w"].shape == (5, 5) and t1["fused_w"].shape == (3, 3)
+    np.testing.assert_array_equal(t1["fused_w"], w.astype(np.float64))
+
+
+@pytest.mark.parametrize("kwargs,code", [
+    (dict(dims=(0, 64)), 1), (dict(dtype=9), 1), (dict(bc=5), 1),
+    (dict(dims=(1, 64)), 2), (dict(fusion_depth=-1), 1)])
+def test_plan_rejects_bad_arguments(lib, kwargs, code):
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
+    args = dict(dims=(64, 64), dtype="bf16", bc="periodic", fusion_depth=1)
+    args.update(kwargs)
+    with pytest.raises(binding.SparStencilError) as e:
+        binding.Plan(w, **args)
+    assert e.value.code == code
+
+
+def test_binding_checks_rank(lib):
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
+    with pytest.raises(ValueError):
+        binding.Plan(w, (64, 64, 64))
+
+
+def test_star_plan_rejects_off_axis_weight(lib):
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
+    with pytest.raises(binding.SparStencilError) as e:
+        binding.Plan(w, (64, 64), shape="star")
+    assert e.value.code == 1
+
+
+def test_cost_model_orders_layouts():
+    """Sec. 3.3 cost model sanity: the crushed layout moves fewer shared-memory bytes than
+    plain flattening (r1 = r2 = 1), in the oracle's own morph dimensions."""
+    mp1, kp1, np1 = morph.morph_dims(3, 1, 1, 4098, 4098)
+    mp2, kp2, np2 = morph.morph_dims(3, 16, 8, 4098, 4098)
+    trans1 = kp1 * (mp1 / 2 + np1)
+    trans2 = kp2 * (mp2 / 2 + np2)
+    assert trans2 < trans1 / 5
