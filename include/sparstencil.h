@@ -113,6 +113,22 @@ sparstencil_status sparstencil_run_profiled(sparstencil_plan_t plan, const float
                                             cudaStream_t stream, double* copy_in_ms, double* sweeps_ms,
                                             int* num_sweeps);
 
+/* Allocation-free variant of sparstencil_run, for callers that cannot call cudaMalloc:
+ * services that forbid device allocation once running (cudaMalloc can synchronise the
+ * device) and processes whose device memory belongs to a framework allocator with a fixed
+ * budget.  The paper has no counterpart; this is a deployment convenience.
+ *   plan, in, out, timesteps, stream: as for sparstencil_run (in and out stay caller-owned).
+ * Instead of the plan's workspace it uses two file-scope static device arrays that every
+ * GPU loading the library holds until exit: 32 MiB of ping-pong grids (at most 4,194,304
+ * padded cells per grid, e.g. a 2040 x 2040 grid with ghost width 4) and 512 KiB of
+ * planner tables.  Larger grids are rejected with SPST_ERR_UNSUPPORTED and a message.
+ * It calls no cudaMalloc, cudaFree or allocating library routine; the first call on a
+ * device resolves the arrays' device addresses (cudaGetSymbolAddress) and should come
+ * before any stream capture.  All calls share the arrays: each call clears what must
+ * start at zero and re-uploads its tables, and calls that overlap on the GPU race. */
+sparstencil_status sparstencil_run_noalloc(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
+                                           cudaStream_t stream);
+
 /* Releases the plan and every device buffer the library allocated for it. */
 sparstencil_status sparstencil_plan_destroy(sparstencil_plan_t plan);
 

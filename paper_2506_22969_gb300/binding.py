@@ -39,7 +39,8 @@ class PlanInfo(ctypes.Structure):
                 ("ghost", ctypes.c_int), ("tile_pitch", ctypes.c_int), ("tile_rows", ctypes.c_int)]
 
 
-EXPORTS = ["sparstencil_plan", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host", "sparstencil_plan_destroy",
+EXPORTS = ["sparstencil_plan", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host",
+           "sparstencil_run_noalloc", "sparstencil_plan_destroy",
            "sparstencil_workspace_bytes", "sparstencil_bind_workspace", "sparstencil_run_batch", "sparstencil_query",
            "sparstencil_plan_tables", "sparstencil_table_kpad", "sparstencil_direct_run", "sparstencil_error_norms",
            "sparstencil_device_status", "sparstencil_set_wait_limit_ns", "sparstencil_last_error",
@@ -62,6 +63,7 @@ def load():
     lib.sparstencil_run.argtypes = [vp, vp, vp, i64, vp]
     lib.sparstencil_run_host.argtypes = [vp, vp, vp, i64, vp]
     lib.sparstencil_run_profiled.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.sparstencil_run_noalloc.argtypes = [vp, vp, vp, i64, vp]
     lib.sparstencil_plan_destroy.argtypes = [vp]
     lib.sparstencil_workspace_bytes.argtypes = [vp]
     lib.sparstencil_workspace_bytes.restype = ctypes.c_size_t
@@ -151,6 +153,11 @@ class Plan:
 
     def run(self, x, out, steps: int, stream=None):
         _check(load().sparstencil_run(self._h, _dev_ptr(x), _dev_ptr(out), int(steps), _stream_ptr(stream)))
+        return out
+
+    def run_noalloc(self, x, out, steps: int, stream=None):
+        """sparstencil_run_noalloc: same result as run(), no device allocation (static scratch)."""
+        _check(load().sparstencil_run_noalloc(self._h, _dev_ptr(x), _dev_ptr(out), int(steps), _stream_ptr(stream)))
         return out
 
     def run_profiled(self, x, out, steps: int, stream=None):

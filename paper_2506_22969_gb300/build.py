@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsparstencil.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-CU_SOURCES = ["sweep2d.cu", "aux.cu"]
+CU_SOURCES = ["sweep2d.cu", "aux.cu", "noalloc.cu"]
 CPP_SOURCES = ["planner.cpp", "capi.cpp"]
 HEADERS = ["kernels.h", "planner.h"]
 

@@ -317,6 +317,148 @@ bool shape_mask_ok(sparstencil_shape shape, int ndim, int r, const float* w) {
 
 }  // namespace
 
+
+// ---------------------------------------------------------------------------------------
+// Runs with caller-provided device buffers and no allocation (used by the allocation-free
+// entry point in noalloc.cu): scratch holds the two padded grids, tables the device copies
+// of the planner tables (half for the full sweep, half for the remainder sweep).
+// ---------------------------------------------------------------------------------------
+namespace spst {
+
+sparstencil_status report_error(sparstencil_status s, const char* msg) { return fail(s, msg); }
+
+sparstencil_status run_plan_with_buffers(sparstencil_plan_t p, const float* in, float* out, int64_t T,
+                                         cudaStream_t stream, float* scratch, size_t scratch_floats,
+                                         uint32_t* tables, size_t table_words) {
+  if (!p || !in || !out) return fail(SPST_ERR_INVALID, "null plan or grid");
+  if (T < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
+  if (in == out) return fail(SPST_ERR_INVALID, "in and out must not alias");
+  int dev = 0, major = 0, minor = 0, sms = 0;
+  SPST_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  SPST_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev), "device attribute");
+  SPST_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev), "device attribute");
+  SPST_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  if (major != 10 || minor != 3) return fail(SPST_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300)");
+  const PlanGeometry& g = p->geo;
+  const size_t grid = ((size_t)g.Hp * (size_t)g.Wp + 63) & ~(size_t)63;  // 256-byte aligned grids
+  if (2 * grid > scratch_floats)
+    return fail(SPST_ERR_UNSUPPORTED, "grid too large for the allocation-free path: needs " + std::to_string(grid) +
+                                          " padded cells per ping-pong grid, the static scratch holds " +
+                                          std::to_string(scratch_floats / 2));
+  if (T == 0) {
+    SPST_CUDA(cudaMemcpyAsync(out, in, (size_t)g.H * g.W * 4, cudaMemcpyDeviceToDevice, stream), "copy in->out");
+    return SPST_OK;
+  }
+  std::vector<int> sweeps((size_t)(T / p->t), p->t);
+  if (T % p->t) sweeps.push_back((int)(T % p->t));
+  // device copies of the tables of each sweep depth used (at most two)
+  struct Region {
+    int depth;
+    const SweepTables* T;
+    int32_t* lut;
+    uint32_t* a_words;
+    uint32_t* meta;
+  } regions[2];
+  int nreg = 0;
+  const size_t half_words = table_words / 2;
+  for (int depth : sweeps) {
+    bool seen = false;
+    for (int r = 0; r < nreg; r++) seen |= regions[r].depth == depth;
+    if (seen) continue;
+    std::string err;
+    const SweepTables* Tt = tables_for(p, depth, &err);
+    if (!Tt) return fail(SPST_ERR_UNSUPPORTED, err);
+    const size_t need = Tt->lut.size() + Tt->a_words.size() + Tt->meta_words.size();
+    if (need > half_words) return fail(SPST_ERR_UNSUPPORTED, "planner tables too large for the static table area");
+    uint32_t* base = tables + (size_t)nreg * half_words;
+    Region& rg = regions[nreg++];
+    rg.depth = depth;
+    rg.T = Tt;
+    rg.lut = (int32_t*)base;
+    rg.a_words = base + Tt->lut.size();
+    rg.meta = rg.a_words + Tt->a_words.size();
+    SPST_CUDA(cudaMemcpyAsync(rg.lut, Tt->lut.data(), Tt->lut.size() * 4, cudaMemcpyHostToDevice, stream), "lut");
+    SPST_CUDA(cudaMemcpyAsync(rg.a_words, Tt->a_words.data(), Tt->a_words.size() * 4, cudaMemcpyHostToDevice, stream),
+              "A''");
+    SPST_CUDA(cudaMemcpyAsync(rg.meta, Tt->meta_words.data(), Tt->meta_words.size() * 4, cudaMemcpyHostToDevice,
+                              stream),
+              "metadata");
+  }
+  float* pad[2] = {scratch, scratch + grid};
+  CUtensorMap tm[2];
+  EncodeTiledFn enc = get_encode_tiled();
+  if (!enc) return fail(SPST_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  for (int i = 0; i < 2; i++) {
+    cuuint64_t gdim[2] = {(cuuint64_t)g.Wp, (cuuint64_t)g.Hp};
+    cuuint64_t gstr[1] = {(cuuint64_t)g.Wp * 4};
+    cuuint32_t box[2] = {(cuuint32_t)g.P, (cuuint32_t)g.box_h};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(&tm[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pad[i], gdim, gstr, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SPST_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  }
+  int* status = device_status_word();
+  if (!status) return fail(SPST_ERR_CUDA, "device status word unavailable");
+  // the static arrays keep the previous call's contents: the second grid's ghost cells and
+  // slack columns must start at zero (the copy-in writes every cell of the first grid)
+  SPST_CUDA(cudaMemsetAsync(pad[1], 0, grid * 4, stream), "clear scratch");
+  SPST_CUDA(launch_pad_copy2d(in, pad[0], (int)g.H, (int)g.W, g.G, g.Wp, p->bc == SPST_PERIODIC ? 1 : 0, stream),
+            "pad copy");
+  int cur = 0;
+  for (size_t i = 0; i < sweeps.size(); i++) {
+    const Region* rg = nullptr;
+    for (int r = 0; r < nreg; r++)
+      if (regions[r].depth == sweeps[i]) rg = &regions[r];
+    const SweepTables* T_ = rg->T;
+    const bool last = (i + 1 == sweeps.size());
+    Sweep2DParams prm;
+    std::memset(&prm, 0, sizeof(prm));
+    prm.H = (int)g.H;
+    prm.W = (int)g.W;
+    prm.G = g.G;
+    prm.tiles_x = (int)g.tiles_x;
+    prm.tiles_y = (int)g.tiles_y;
+    prm.num_tiles = (int)g.num_tiles;
+    prm.P = g.P;
+    prm.box_h = g.box_h;
+    prm.kpad = T_->kpad;
+    prm.kchunks = T_->kpad / 32;
+    prm.a_pieces = T_->a_pieces;
+    prm.b_pieces = is_split(p->dtype) ? 2 : 1;
+    prm.nterms = 0;
+    prm.term_a[prm.nterms] = 0;
+    prm.term_b[prm.nterms++] = 0;
+    if (prm.b_pieces == 2) {
+      prm.term_a[prm.nterms] = 0;
+      prm.term_b[prm.nterms++] = 1;
+    }
+    for (int pc = 1; pc < T_->a_pieces; pc++) {
+      prm.term_a[prm.nterms] = pc;
+      prm.term_b[prm.nterms++] = 0;
+    }
+    prm.nacc = tmem_accumulators(*T_);
+    prm.fp16 = word_of(p->dtype) == Word::FP16 ? 1 : 0;
+    prm.wscale = std::ldexp(1.0f, -T_->wscale_log2);
+    prm.lut = rg->lut;
+    prm.a_words = rg->a_words;
+    prm.meta_words = rg->meta;
+    prm.S_hi = T_->S_hi;
+    prm.S_lo = T_->S_lo;
+    prm.out = last ? out : pad[1 - cur];
+    prm.out_pitch = last ? g.W : g.Wp;
+    prm.out_off = last ? 0 : g.G;
+    prm.out_ghost = (!last && p->bc == SPST_PERIODIC) ? 1 : 0;
+    prm.status = status;
+    prm.wait_ns = g_wait_ns;
+    SPST_CUDA(launch_sweep2d(tm[cur], prm, sms, stream), "sweep launch");
+    cur = 1 - cur;
+  }
+  return SPST_OK;
+}
+
+}  // namespace spst
+
 extern "C" {
 
 const char* sparstencil_last_error(void) { return g_last_error.c_str(); }
