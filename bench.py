@@ -204,6 +204,43 @@ def ncu_case(spec: str, t: int):
     assert binding.device_status() == 0
 
 
+def trace_case():
+    """Prints the CTA-0 timeline (microseconds from the first TMA issue) of one sweep for
+    each precision and fused depth of the workload.  Needs a library built with
+    SPARSTENCIL_DEBUG_TRACE=1."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_22969_gb300 import binding
+    cfg, w, u = _workload()
+    x = torch.from_numpy(u).cuda()
+    y = torch.empty_like(x)
+    for dtype in ("bf16_split", "bf16"):
+        for t in (1, 2, 3):
+            plan = binding.Plan(w, cfg["dims"], dtype=dtype, bc=cfg["bc"], fusion_depth=t, shape=cfg["shape"])
+            plan.run(x, y, t)
+            torch.cuda.synchronize()
+            binding.trace(True)
+            c_ms, s_ms, n = plan.run_profiled(x, y, t)
+            tr, ch = binding.trace_read()
+            binding.trace(False)
+            t0 = int(np.min(tr[tr > 0])) if np.any(tr > 0) else 0
+            ntile = int(np.sum(tr[1, :, 0] > 0))
+            print(f"== {dtype} t={t}: sweep {s_ms * 1e3:.1f} us, CTA 0 tiles {ntile}")
+            names = ["tma", "mma", "gather", "epi"]
+            for li in range(ntile):
+                row = " ".join(f"{names[r]} {(tr[r, li, 0] - t0) / 1e3:7.2f}-{(tr[r, li, 1] - t0) / 1e3:7.2f}"
+                               if tr[r, li, 1] else (f"{names[r]} {(tr[r, li, 0] - t0) / 1e3:7.2f}"
+                                                     if tr[r, li, 0] else f"{names[r]}    -   ")
+                               for r in range(4))
+                print(f"  tile {li}: {row}")
+            c0 = ch[0, 0]
+            for kc in range(16):
+                if ch[kc, 0]:
+                    print(f"  tile 1 chunk {kc}: start {ch[kc, 0] - c0:6d} loaded {ch[kc, 1] - c0:6d} "
+                          f"slot-free {ch[kc, 2] - c0:6d} published {ch[kc, 3] - c0:6d} (cycles)")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,6 +249,8 @@ def main():
     ap.add_argument("--impl", default="sparstencil", choices=["sparstencil", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fusion", type=int, default=0, help="fusion depth t (0: autotune over 1..3)")
+    ap.add_argument("--trace", action="store_true",
+                    help="print the sweep kernel's CTA-0 timeline for single sweeps of the workload and exit")
     ap.add_argument("--ncu-case", default=None,
                     help="profiling case for ncu: '<precision>:<side>' runs a few single sweeps of Box-2D9P "
                          "on a side x side periodic grid and exits (no JSON line)")
@@ -220,6 +259,8 @@ def main():
         return run_reference(args)
     if args.ncu_case:
         return ncu_case(args.ncu_case, args.fusion or 1)
+    if args.trace:
+        return trace_case()
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -259,15 +300,23 @@ def main():
             ts.append(e0.elapsed_time(e1))
         return ts
 
-    # autotune the fusion depth (the paper's layout search rebuilt as a measured search)
+    # autotune the fusion depth per precision (the paper's layout search rebuilt as a
+    # measured search over the fused depth t)
     candidates = [args.fusion] if args.fusion > 0 else [1, 2, 3]
-    best = None
-    for t in candidates:
-        plan = binding.Plan(w, (H, W), dtype="bf16_split", bc=cfg["bc"], fusion_depth=t, shape=cfg["shape"])
-        ms = min(timed_runs(lambda: plan.run(x, y, T), 2, 1))
-        if best is None or ms < best[1]:
-            best = (t, ms, plan)
-    t_best, _, plan = best
+    tune = {}
+
+    def autotune(dtype):
+        best = None
+        tune[dtype] = {}
+        for t in candidates:
+            pl = binding.Plan(w, (H, W), dtype=dtype, bc=cfg["bc"], fusion_depth=t, shape=cfg["shape"])
+            ms = min(timed_runs(lambda: pl.run(x, y, T), 2, 1))
+            tune[dtype][str(t)] = ms
+            if best is None or ms < best[1]:
+                best = (t, ms, pl)
+        return best
+
+    t_best, _, plan = autotune("bf16_split")
     info = plan.info()
 
     # accuracy of the timed configuration (sampled points against the dependence-cone oracle)
@@ -330,7 +379,7 @@ def main():
     e2e_val = world * len(e2e_ms) * pts / (sum(e2e_ms) / 1e3) / 1e9
 
     # variants: single-word BF16 and the plain FP32 CUDA-core direct stencil
-    plan1 = binding.Plan(w, (H, W), dtype="bf16", bc=cfg["bc"], fusion_depth=t_best, shape=cfg["shape"])
+    t1, _, plan1 = autotune("bf16")
     ms1 = timed_runs(lambda: plan1.run(x, y, T), max(2, args.steps // 2), 1)
     rel_single = sampled_rel_l2(y)
     work = torch.empty_like(x)
@@ -340,7 +389,7 @@ def main():
         "bf16_split_sparse_tc": {"gstencil_s": args.steps * pts / (tot / 1e3) / 1e9, "rel_l2_sampled": rel_split,
                                  "fusion_depth": t_best},
         "bf16_single_sparse_tc": {"gstencil_s": pts / (statistics.median(ms1) / 1e3) / 1e9,
-                                  "rel_l2_sampled": rel_single, "fusion_depth": t_best},
+                                  "rel_l2_sampled": rel_single, "fusion_depth": t1},
         "fp32_direct_cuda_core": {"gstencil_s": pts / (statistics.median(msd) / 1e3) / 1e9,
                                   "rel_l2_sampled": rel_direct, "fusion_depth": 1},
     }
@@ -368,6 +417,7 @@ def main():
             "gpu_launches": args.steps * (1 + nsw),
             "clocks": clock_info,
             "variants": variants,
+            "autotune_ms_per_run": tune,
             "rel_l2_sampled": rel_split,
             "device_status": status,
             "planner_ms": info.planner_ms,

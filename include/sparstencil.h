@@ -72,6 +72,8 @@ typedef struct {
   int ghost;           /* ghost width G of the padded ping-pong grids (= largest fused radius) */
   int tile_pitch;      /* floats per row of the shared-memory halo tile (TMA box width) */
   int tile_rows;       /* rows of the halo tile (TMA box height) */
+  int bank_conflicts;  /* residue repeats left by the planner's chunk packing (0: the B'' gather
+                          reads shared memory without bank conflicts) */
 } sparstencil_plan_info;
 
 /* Builds a plan for `shape` stencils of radius `radius` on an ndim grid of extents dims.
@@ -189,6 +191,21 @@ sparstencil_status sparstencil_device_status(cudaStream_t stream);
 /* Sets the bound (nanoseconds) of every device-side wait; 0 restores the default (2 s).
  * Host only; applies to launches made after the call. */
 sparstencil_status sparstencil_set_wait_limit_ns(uint64_t ns);
+
+/* Debugging aid, present only in libraries built with tracing (build.py with the
+ * environment variable SPARSTENCIL_DEBUG_TRACE=1; otherwise SPST_ERR_UNSUPPORTED, because the
+ * stamps slow the sweep by ~15%): enable (1) or disable (0) the sweep kernel's timeline
+ * trace on the current device.  When enabled, CTA 0 of each sweep records %globaltimer stamps (nanoseconds) for
+ * its first 64 tiles: per role (0 TMA producer, 1 MMA issuer, 2 first B'' gather warp,
+ * 3 first epilogue warp) the time its first wait for the tile completed and the time it
+ * finished the tile.  Enabling clears the buffer.  Synchronous; not for timed runs. */
+sparstencil_status sparstencil_trace(int enable);
+
+/* Copies up to n trace entries to host memory; synchronous.  Entries 0..511: layout
+ * [role][tile][start, end] (4 x 64 x 2, nanoseconds); entries 512..575: clock64 stamps of
+ * the first gather warp's K chunks of CTA 0's second tile, [chunk < 16][chunk start, halo
+ * values loaded, chunk slot free, chunk published]. */
+sparstencil_status sparstencil_trace_read(uint64_t* out, int n);
 
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char* sparstencil_last_error(void);

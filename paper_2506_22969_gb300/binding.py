@@ -36,14 +36,16 @@ class PlanInfo(ctypes.Structure):
                 ("r1", ctypes.c_int), ("r2", ctypes.c_int), ("r3", ctypes.c_int), ("kprime", ctypes.c_int),
                 ("kpad", ctypes.c_int), ("zero_columns", ctypes.c_int), ("mma_terms", ctypes.c_int),
                 ("tile_outputs", ctypes.c_int), ("num_tiles", ctypes.c_int64), ("planner_ms", ctypes.c_double),
-                ("ghost", ctypes.c_int), ("tile_pitch", ctypes.c_int), ("tile_rows", ctypes.c_int)]
+                ("ghost", ctypes.c_int), ("tile_pitch", ctypes.c_int), ("tile_rows", ctypes.c_int),
+                ("bank_conflicts", ctypes.c_int)]
 
 
 EXPORTS = ["sparstencil_plan", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host",
            "sparstencil_run_noalloc", "sparstencil_plan_destroy",
            "sparstencil_workspace_bytes", "sparstencil_bind_workspace", "sparstencil_run_batch", "sparstencil_query",
            "sparstencil_plan_tables", "sparstencil_table_kpad", "sparstencil_direct_run", "sparstencil_error_norms",
-           "sparstencil_device_status", "sparstencil_set_wait_limit_ns", "sparstencil_last_error",
+           "sparstencil_device_status", "sparstencil_set_wait_limit_ns", "sparstencil_trace",
+           "sparstencil_trace_read", "sparstencil_last_error",
            "sparstencil_version"]
 
 _lib = None
@@ -76,6 +78,8 @@ def load():
     lib.sparstencil_error_norms.argtypes = [vp, vp, i64, vp, vp]
     lib.sparstencil_device_status.argtypes = [vp]
     lib.sparstencil_set_wait_limit_ns.argtypes = [ctypes.c_uint64]
+    lib.sparstencil_trace.argtypes = [i32]
+    lib.sparstencil_trace_read.argtypes = [vp, i32]
     lib.sparstencil_last_error.restype = ctypes.c_char_p
     lib.sparstencil_version.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -233,6 +237,19 @@ def device_status(stream=None) -> int:
 
 def set_wait_limit_ns(ns: int):
     _check(load().sparstencil_set_wait_limit_ns(int(ns)))
+
+
+def trace(enable: bool):
+    """Enables/disables the sweep kernel's CTA-0 timeline trace (clears it)."""
+    _check(load().sparstencil_trace(1 if enable else 0))
+
+
+def trace_read():
+    """(tiles, chunks): tiles = int64 [role(TMA, MMA, gather, epilogue)][tile<64][start, end]
+    in ns; chunks = int64 [chunk<16][start, loaded, slot free, published] in clock cycles."""
+    out = np.zeros(4 * 64 * 2 + 64, np.uint64)
+    _check(load().sparstencil_trace_read(out.ctypes.data, out.size))
+    return out[:512].reshape(4, 64, 2).astype(np.int64), out[512:].reshape(16, 4).astype(np.int64)
 
 
 def run_batch(plans, xs, outs, steps, stream=None):

@@ -37,6 +37,8 @@ def _nvcc() -> str:
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
+if os.environ.get("SPARSTENCIL_DEBUG_TRACE") == "1":  # sweep timeline stamps (debugging only)
+    NVCC_FLAGS = NVCC_FLAGS + ["-DSPST_TRACE=1"]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function"]
 
 

@@ -527,8 +527,10 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
     probe.P = g.P;
     probe.box_h = g.box_h;
     probe.kpad = p->full.kpad;
+    probe.kchunks = p->full.kpad / 32;
+    probe.a_pieces = p->full.a_pieces;
     probe.b_pieces = is_split(dtype) ? 2 : 1;
-    if (spst::sweep2d_smem_bytes(probe) > 232448)
+    if (!spst::sweep2d_fits(probe))
       return fail(SPST_ERR_UNSUPPORTED, "halo tile of the fused radius does not fit in shared memory");
   }
   p->planner_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -646,6 +648,7 @@ sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_i
   info->ghost = plan->geo.G;
   info->tile_pitch = plan->geo.P;
   info->tile_rows = plan->geo.box_h;
+  info->bank_conflicts = plan->full.bank_conflicts;
   return SPST_OK;
 }
 
@@ -735,6 +738,20 @@ sparstencil_status sparstencil_error_norms(const float* x, const float* ref, int
   SPST_CUDA(spst::launch_error_norms(x, ref, n, acc, stream), "norm kernel");
   SPST_CUDA(cudaMemcpyAsync(out_host, acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), "norm D2H");
   SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_trace(int enable) {
+  const cudaError_t e = spst::sweep_trace_enable(enable ? 1 : 0);
+  if (e == cudaErrorNotSupported)
+    return fail(SPST_ERR_UNSUPPORTED, "library built without tracing (set SPARSTENCIL_DEBUG_TRACE=1 when building)");
+  SPST_CUDA(e, "trace enable");
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_trace_read(uint64_t* out, int n) {
+  if (!out || n < 0) return fail(SPST_ERR_INVALID, "bad trace buffer");
+  SPST_CUDA(spst::sweep_trace_read((unsigned long long*)out, n), "trace read");
   return SPST_OK;
 }
 

@@ -8,9 +8,9 @@
 
 namespace spst {
 
-constexpr int kSweepThreads = 512;   // 16 warps: TMA, MMA, 2 spare, 4 epilogue, 8 gather
+constexpr int kSweepThreads = 768;   // 24 warps: TMA, MMA, 2 spare, 4 epilogue, 16 gather
 constexpr int kHaloStages = 2;
-constexpr int kBSlots = 3;
+constexpr int kMaxBSlots = 8;        // ring of B'' K chunks (the launcher fills the shared memory left)
 constexpr int kPieceBytes = 16 * 576;  // one K-chunk (32 x 128, 16-bit) of B' in the padded K-major layout
 constexpr int kLBO = 144;              // bytes between K-adjacent core matrices
 constexpr int kSBO = 576;              // bytes between 8-patch groups
@@ -26,6 +26,8 @@ struct Sweep2DParams {
   int nterms;           // MMAs per K chunk; term i multiplies A piece term_a[i] by B piece term_b[i]
   int term_a[4], term_b[4];
   int nacc;             // TMEM accumulators (2: the epilogue of one tile overlaps the next tile's MMAs)
+  int nslots;           // B'' chunk slots in shared memory (1..kMaxBSlots; set by launch_sweep2d)
+  int early_tma;        // 1: tile 0's halo load is issued before the set-up (set by launch_sweep2d)
   int fp16;             // operand type: 1 = FP16, 0 = BF16
   float wscale;         // 2^-s: the weight pieces hold w * 2^s
   const int32_t* lut;         // [kpad] tile-word offsets (device)
@@ -40,10 +42,20 @@ struct Sweep2DParams {
   unsigned long long wait_ns;  // bound of every device-side wait
 };
 
-// Shared-memory bytes the sweep kernel needs for this geometry.
+// Shared-memory bytes the sweep kernel needs for this geometry (with p.nslots chunk slots).
 size_t sweep2d_smem_bytes(const Sweep2DParams& p);
+// Largest chunk-slot count (<= kMaxBSlots) that fits the per-CTA shared memory, or 0.
+int sweep2d_max_slots(const Sweep2DParams& p);
+// Whether the sweep kernel fits shared memory for this geometry (halo stages, >= 2 chunk
+// slots, and the set-up staging of A'' and the metadata).
+bool sweep2d_fits(const Sweep2DParams& p);
 // Launches one sparse sweep (grid = min(num_tiles, SMs)); returns the launch error.
 cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p, int num_sms, cudaStream_t stream);
+
+// Timeline trace of CTA 0 of the sweep kernel (debugging aid): enable/disable (clears the
+// buffer) and read up to n entries ([role][tile][start, end], roles TMA, MMA, gather, epilogue).
+cudaError_t sweep_trace_enable(int on);
+cudaError_t sweep_trace_read(unsigned long long* out, int n);
 
 // Copies an unpadded H x W grid into a padded (H+2G) x Wp grid: interior, ghosts (periodic
 // images or zeros) and the slack columns (zeros).

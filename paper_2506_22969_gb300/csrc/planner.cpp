@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 
 namespace spst {
 
@@ -143,6 +144,170 @@ std::vector<std::pair<int, int>> hierarchical_matching(int n, int g, int k) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Packing matched pairs into K chunks of `slots` (16) pairs so that, within every chunk,
+// the first-column offsets and the second-column offsets are distinct mod 16 (see the
+// gather's bank rule in build_sweep_tables_2d).  View each pair as an edge between its
+// first column's residue (left vertex) and its second column's residue (right vertex) of
+// a bipartite multigraph on 16 + 16 vertices; a conflict-free chunk is a matching, so the
+// packing is an edge colouring.  Steps: orient each pair (swap its columns) to keep every
+// residue's degree small, then colour the edges with max-degree colours by alternating-
+// path recolouring (Konig's edge-colouring theorem for bipartite graphs), one chunk per
+// colour, and fill each chunk with padding pairs (zero columns) of the unused residues.
+// Returns 0, or -1 (order/lut untouched) when no conflict-free packing uses the minimum
+// number of chunks (some residue is carried by more than twice that many columns).
+// ---------------------------------------------------------------------------------------
+int arrange_pairs(const std::vector<std::pair<int, int>>& pairs, const std::vector<std::pair<int, int>>& offs,
+                  int slots, std::vector<int>* order_out, std::vector<int32_t>* lut_out) {
+  const int n = (int)pairs.size();
+  auto res = [](int o) { return ((o % 16) + 16) % 16; };
+  // orientation: every residue v needs out(v) <= D and in(v) <= D, where out counts the
+  // pairs whose first column has residue v and in those whose second column has.  Choosing
+  // which column goes first is a degree-constrained orientation: each pair gives one "out"
+  // to one of its two residues, and v must receive between lo(v) = max(0, deg(v) - D) and
+  // D of them (deg counts both columns).  Solved as a bipartite b-matching by augmenting
+  // paths: first up to lo(v) per residue, then up to D; D starts at the chunk minimum and
+  // grows until every pair is placed with every lower bound met.
+  std::vector<int> X(n), Y(n);
+  for (int i = 0; i < n; i++) {
+    X[i] = res(offs[i].first);
+    Y[i] = res(offs[i].second);
+  }
+  std::vector<int> owner(n, -1);  // residue that takes the pair's "out" (its first column)
+  const int D = std::max(1, (n + slots - 1) / slots);
+  {
+    int deg[16] = {0};
+    for (int i = 0; i < n; i++) {
+      deg[X[i]]++;
+      deg[Y[i]]++;
+    }
+    int load[16] = {0}, cap[16];
+    std::fill(owner.begin(), owner.end(), -1);
+    // augmenting path search: place pair e on residue v or move another pair off v
+    std::function<bool(int, std::vector<char>&)> place = [&](int e, std::vector<char>& seen) -> bool {
+      const int cand[2] = {X[e], Y[e]};
+      for (int k = 0; k < 2; k++) {
+        const int v = cand[k];
+        if (k == 1 && Y[e] == X[e]) break;
+        if (seen[v]) continue;
+        seen[v] = 1;
+        if (load[v] < cap[v]) {
+          owner[e] = v;
+          load[v]++;
+          return true;
+        }
+        for (int f = 0; f < n; f++) {
+          if (owner[f] != v || f == e) continue;
+          const int other = (X[f] == v) ? Y[f] : X[f];
+          if (other == v) continue;
+          owner[f] = -1;
+          load[v]--;
+          if (place(f, seen)) {
+            owner[e] = v;
+            load[v]++;
+            return true;
+          }
+          owner[f] = v;
+          load[v]++;
+        }
+      }
+      return false;
+    };
+    bool ok = true;
+    for (int v = 0; v < 16; v++) ok &= deg[v] <= 2 * D;  // lo(v) <= D is needed
+    if (!ok) return -1;  // no conflict-free packing in the minimum number of chunks
+    for (int phase = 0; phase < 2 && ok; phase++) {
+      for (int v = 0; v < 16; v++) cap[v] = phase == 0 ? std::max(0, deg[v] - D) : D;
+      for (int e = 0; e < n; e++) {
+        if (owner[e] >= 0) continue;
+        std::vector<char> seen(16, 0);
+        if (!place(e, seen) && phase == 1) ok = false;
+      }
+      if (phase == 0)
+        for (int v = 0; v < 16; v++) ok &= load[v] >= std::max(0, deg[v] - D);
+    }
+    if (!ok) return -1;
+  }
+  std::vector<int> L(n), Rr(n);
+  std::vector<char> swp(n, 0);
+  for (int i = 0; i < n; i++) {
+    swp[i] = owner[i] != X[i];
+    L[i] = owner[i];
+    Rr[i] = swp[i] ? X[i] : Y[i];
+  }
+  // colouring: atL[v][c] / atR[v][c] = edge of colour c at vertex v (-1 none)
+  std::vector<std::vector<int>> atL(16, std::vector<int>(D, -1)), atR(16, std::vector<int>(D, -1));
+  std::vector<int> col(n, -1);
+  for (int e = 0; e < n; e++) {
+    const int u = L[e], v = Rr[e];
+    int a = 0, b = 0;
+    while (atL[u][a] >= 0) a++;  // free at u (exists: deg(u) <= D)
+    while (atR[v][b] >= 0) b++;  // free at v
+    if (atR[v][a] >= 0) {
+      // swap colours a and b along the alternating path that starts at v with colour a; it
+      // cannot reach u (bipartite parity), so afterwards a is free at both u and v
+      std::vector<int> path;
+      int side = 1, vert = v, cc = a;  // side 1: right vertex
+      while (true) {
+        const int f = side ? atR[vert][cc] : atL[vert][cc];
+        if (f < 0) break;
+        path.push_back(f);
+        vert = side ? L[f] : Rr[f];
+        side = 1 - side;
+        cc = (cc == a) ? b : a;
+      }
+      for (int f : path) {
+        atL[L[f]][col[f]] = -1;
+        atR[Rr[f]][col[f]] = -1;
+      }
+      for (int f : path) {
+        col[f] = (col[f] == a) ? b : a;
+        atL[L[f]][col[f]] = f;
+        atR[Rr[f]][col[f]] = f;
+      }
+    }
+    col[e] = a;
+    atL[u][a] = e;
+    atR[v][a] = e;
+  }
+  std::vector<int>& order = *order_out;
+  std::vector<int32_t>& lut = *lut_out;
+  order.clear();
+  lut.clear();
+  int repeats = 0;
+  for (int c = 0; c < D; c++) {
+    int ua[16] = {0}, ub[16] = {0}, cnt = 0;
+    for (int e = 0; e < n; e++) {
+      if (col[e] != c) continue;
+      int a = pairs[e].first, b = pairs[e].second, oa = offs[e].first, ob = offs[e].second;
+      if (swp[e]) {
+        std::swap(a, b);
+        std::swap(oa, ob);
+      }
+      order.push_back(a);
+      order.push_back(b);
+      lut.push_back(oa);
+      lut.push_back(ob);
+      if (ua[res(oa)]++) repeats++;
+      if (ub[res(ob)]++) repeats++;
+      cnt++;
+    }
+    // padding pairs: zero columns reading words of the residues the chunk does not use
+    for (int s = cnt; s < slots; s++) {
+      int ra = 0, rb = 0;
+      while (ra < 15 && ua[ra]) ra++;
+      while (rb < 15 && ub[rb]) rb++;
+      ua[ra]++;
+      ub[rb]++;
+      order.push_back(-1);
+      order.push_back(-1);
+      lut.push_back(ra);
+      lut.push_back(rb);
+    }
+  }
+  return repeats;
+}
+
+// ---------------------------------------------------------------------------------------
 // 2D sweep tables.
 // ---------------------------------------------------------------------------------------
 std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, const PlanGeometry& geo, Word word,
@@ -186,7 +351,7 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
 
   // Structured sparsity conversion (Sec. 3.2).
   auto pairs = hierarchical_matching(kp, g, kt);
-  std::vector<int> order;
+  std::vector<std::pair<int, int>> kept;
   for (auto& pr : pairs) {
     bool a_nz = colnz[pr.first];
     bool b_nz = pr.second >= 0 && colnz[pr.second];
@@ -195,10 +360,47 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
       T.dropped_pairs++;
       continue;
     }
-    order.push_back(pr.first);
-    order.push_back(pr.second);
+    kept.push_back(pr);
   }
-  while (order.size() % Tile2D::KCHUNK) order.push_back(-1);
+  // Lookup-table offsets (Sec. 3.3): tile word of column (u, c) relative to the patch base
+  // (py*R2*P + px*R1).  The tile starts G cells before the tile's first output, the patch
+  // window R cells before the patch's first output.  A zero column reads its pair partner
+  // (any finite value works: its weights are zero).
+  auto off = [&](int col) { return (col / g + geo.G - R) * geo.P + (col % g + geo.G - R); };
+  std::vector<std::pair<int, int>> offs;
+  for (auto& pr : kept) offs.push_back({off(pr.first), pr.second >= 0 ? off(pr.second) : off(pr.first)});
+  // Each matched pair holds at most one nonzero per row (its columns are >= kt apart, or one
+  // is a zero column), so any two pairs form a valid group of four: the pairs may be
+  // reordered and each pair's two columns swapped without breaking 2:4.  Use that freedom
+  // for the gather: chunk slot p (pair p of a 32-row K chunk) is read by lane p of both
+  // half-warps, whose patches are 16 words apart, so the loads are free of bank conflicts
+  // when the chunk's 16 first-column offsets, and its 16 second-column offsets, are distinct
+  // mod 16.  arrange_pairs packs the pairs into chunks that way (padding pairs fill the
+  // gaps with offsets of the missing residues).
+  std::vector<int> order;
+  std::vector<int32_t> lut;
+  if (arrange_pairs(kept, offs, Tile2D::KCHUNK / 2, &order, &lut) < 0) {
+    // keep Algorithm 1's order; count the residue repeats the gather will meet
+    order.clear();
+    lut.clear();
+    for (size_t i = 0; i < kept.size(); i++) {
+      order.push_back(kept[i].first);
+      order.push_back(kept[i].second);
+      lut.push_back(offs[i].first);
+      lut.push_back(offs[i].second);
+    }
+    while (order.size() % Tile2D::KCHUNK) {
+      order.push_back(-1);
+      lut.push_back(0);
+    }
+    T.bank_conflicts = 0;
+    for (size_t k0 = 0; k0 < order.size(); k0 += Tile2D::KCHUNK)
+      for (int side = 0; side < 2; side++) {
+        int seen[16] = {0};
+        for (int j = side; j < Tile2D::KCHUNK; j += 2)
+          if (seen[((lut[k0 + j] % 16) + 16) % 16]++) T.bank_conflicts++;
+      }
+  }
   T.order = order;
   const int kpad = (int)order.size();
   T.kpad = kpad;
@@ -303,17 +505,7 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
       }
     }
   }
-  // Lookup table (Sec. 3.3): tile-word offset of each permuted K row relative to the patch's
-  // base (py*R2*P + px*R1).  The tile starts G cells before the tile's first output, the
-  // patch window R cells before the patch's first output.  A zero column reads its pair
-  // partner (any finite value works: its weights are zero).
-  T.lut.assign(kpad, 0);
-  auto off = [&](int col) { return (col / g + geo.G - R) * geo.P + (col % g + geo.G - R); };
-  for (int kap = 0; kap < kpad; kap++) {
-    int col = order[kap];
-    if (col < 0) col = order[kap ^ 1];
-    T.lut[kap] = col >= 0 ? off(col) : 0;
-  }
+  T.lut = lut;
   (void)mb;
   return "";
 }

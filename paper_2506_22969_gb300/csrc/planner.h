@@ -38,6 +38,7 @@ struct SweepTables {
   int kpad = 0;     // K after matching, pair dropping and padding to a multiple of 32
   int zero_cols = 0;       // zero nodes inserted by Algorithm 1
   int dropped_pairs = 0;   // matched pairs whose two columns are both all-zero (removed)
+  int bank_conflicts = 0;  // repeated residues left by the chunk packing (0: conflict-free gather)
   std::vector<double> wfused;     // (2R+1)^ndim composed weights (FP64)
   std::vector<float> wfused32;    // the same rounded to FP32 (the values the pieces split)
   std::vector<int> order;         // kpad: original A' column per permuted position, -1 = zero column
@@ -72,6 +73,12 @@ std::vector<double> compose_weights(const std::vector<double>& w, int ndim, int 
 // order M1 (block p ascending, t ascending) then M2 (block ascending, u ascending);
 // -1 marks an inserted zero node.
 std::vector<std::pair<int, int>> hierarchical_matching(int n, int g, int k);
+
+// Packs matched pairs (with their tile offsets) into the minimum number of K chunks of
+// `slots` pairs such that the gather's loads are free of bank conflicts; fills order/lut
+// (padding pairs are zero columns) and returns 0, or returns -1 when that is impossible.
+int arrange_pairs(const std::vector<std::pair<int, int>>& pairs, const std::vector<std::pair<int, int>>& offs,
+                  int slots, std::vector<int>* order_out, std::vector<int32_t>* lut_out);
 
 // Builds the sweep tables of a 2D stencil (fused cube `wfused` of radius R) for the Tile2D
 // kernel geometry, the ghost width G and tile pitch P of `geo`, and operand encoding `word`.

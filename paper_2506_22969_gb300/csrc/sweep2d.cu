@@ -8,7 +8,7 @@
 // re-planned for Blackwell:
 //   * warp 0 streams 128 x 128-output halo tiles from the padded input grid with TMA
 //     (cp.async.bulk.tensor.2d) into a 2-stage ring;
-//   * warps 8-15 build B'' one 32-row K chunk at a time from the tile through the lookup
+//   * warps 8-23 build B'' one 32-row K chunk at a time from the tile through the lookup
 //     table (Sec. 3.3), subtract a per-patch reference value (so the tensor cores see
 //     deviations, see below), convert to FP16/BF16 (split: hi and lo words) and store
 //     into a 3-slot ring in the UMMA K-major layout;
@@ -87,10 +87,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
   }
 }
 
-// Warp-uniform bounded wait: every lane polls the barrier (so each lane acquires the phase);
-// the give-up decision is lane 0's and is taken by the whole warp.
+// Warp-uniform bounded wait.  SPST_POLL_ALL_LANES = 1: every lane polls the barrier (each
+// lane acquires the phase itself) and the give-up decision is lane 0's; = 0: lane 0 alone
+// waits and the warp synchronises behind it.
+#ifndef SPST_POLL_ALL_LANES
+#define SPST_POLL_ALL_LANES 1
+#endif
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns, volatile int* abort_flag,
                                           int* status) {
+#if SPST_POLL_ALL_LANES
   const uint64_t t0 = gtimer();
   const int lane = threadIdx.x & 31;
   while (true) {
@@ -107,6 +112,13 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_
       return false;
     }
   }
+#else
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, limit_ns, abort_flag, status) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
+#endif
 }
 
 __device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -138,6 +150,55 @@ __device__ __forceinline__ void unpack2(uint32_t v, int fp16, float& lo, float& 
   }
 }
 
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int2 lds_v2_s32(uint32_t a) {
+  int2 v;
+  asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float4 lds_v4_f32(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sts_f32(uint32_t a, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+// Optional timeline trace of CTA 0 (off unless enabled from the host): per role and tile,
+// the %globaltimer when the role's first wait for the tile completed and when it finished
+// the tile.  Layout: [role 0 TMA, 1 MMA, 2 gather warp, 3 epilogue warp][tile < 64][2].
+constexpr int kTraceTiles = 64;
+__device__ int g_trace_on;
+__device__ unsigned long long g_trace[4 * kTraceTiles * 2];
+
+// Built in only with -DSPST_TRACE=1 (the stamps cost ~15% of the sweep's time).
+#ifndef SPST_TRACE
+#define SPST_TRACE 0
+#endif
+__device__ __forceinline__ void trace(bool on, int role, int li, int ev) {
+#if SPST_TRACE
+  if (on && li < kTraceTiles) g_trace[(role * kTraceTiles + li) * 2 + ev] = gtimer();
+#endif
+}
+// Chunk-level clock64 stamps of gather warp 0 in CTA 0 for tile 1: [chunk < 16][4]
+// (chunk start, halo loads issued+LUT, slot free, chunk published).
+__device__ unsigned long long g_trace_chunks[16 * 4];
+__device__ __forceinline__ void trace_chunk(bool on, int kc, int ev) {
+  if (SPST_TRACE && on && kc < 16) {
+    unsigned long long c;
+    asm volatile("mov.u64 %0, %%clock64;" : "=l"(c));
+    g_trace_chunks[kc * 4 + ev] = c;
+  }
+}
+
 struct SmemLayout {
   uint32_t halo_stride, off_b, slot_bytes, off_lut, off_cv, off_bar, total;
   __host__ __device__ explicit SmemLayout(const Sweep2DParams& p) {
@@ -145,7 +206,7 @@ struct SmemLayout {
     halo_stride = (halo + 1023u) & ~1023u;
     off_b = halo_stride * kHaloStages;
     slot_bytes = (uint32_t)p.b_pieces * (uint32_t)kPieceBytes;
-    off_lut = off_b + slot_bytes * kBSlots;
+    off_lut = off_b + slot_bytes * (uint32_t)p.nslots;
     off_cv = off_lut + (((uint32_t)p.kpad * 4u + 15u) & ~15u);
     off_bar = off_cv + 2u * 128u * 4u;
     total = off_bar + 256u;
@@ -153,11 +214,18 @@ struct SmemLayout {
 };
 
 // barrier indices (8 bytes each, from off_bar)
-constexpr int BAR_HFULL = 0, BAR_HEMPTY = 2, BAR_BFULL = 4, BAR_BEMPTY = 7, BAR_AFULL = 10, BAR_AEMPTY = 12,
-              BAR_CVFULL = 14, BAR_FINAL = 16;
-constexpr int BAR_COUNT = 17;  // 136 bytes, below the TMEM slot at +192
+constexpr int BAR_HFULL = 0, BAR_HEMPTY = 2, BAR_BFULL = 4, BAR_BEMPTY = 4 + kMaxBSlots,
+              BAR_AFULL = 4 + 2 * kMaxBSlots, BAR_AEMPTY = BAR_AFULL + 2, BAR_CVFULL = BAR_AEMPTY + 2,
+              BAR_FINAL = BAR_CVFULL + 2;
+constexpr int BAR_COUNT = BAR_FINAL + 1;  // 27 barriers = 216 bytes, below the TMEM slot at +224
+static_assert(BAR_COUNT * 8 <= 224, "barrier area overlaps the TMEM slot");
 constexpr uint32_t TMEM_COLS = 512;
 
+constexpr int kGatherWarp0 = 8;                                 // warps 8 .. 23 build B''
+constexpr int kGatherWarps = kSweepThreads / 32 - kGatherWarp0;  // 16
+constexpr int kItems = 64 / kGatherWarps;                        // patch pairs per gather warp per chunk
+
+template <int FP16, int SPLIT>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep2d_kernel(const __grid_constant__ CUtensorMap tmap_in, const Sweep2DParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -168,10 +236,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t bar0 = sbase + L.off_bar;
   auto bar = [&](int i) -> uint32_t { return bar0 + 8u * (uint32_t)i; };
-  uint32_t* tmem_slot = (uint32_t*)(smem + L.off_bar + 192);               // 16-byte aligned
-  volatile int* abort_flag = (volatile int*)(smem + L.off_bar + 208);
+  uint32_t* tmem_slot = (uint32_t*)(smem + L.off_bar + 224);               // 16-byte aligned
+  volatile int* abort_flag = (volatile int*)(smem + L.off_bar + 240);
   int32_t* lut_s = (int32_t*)(smem + L.off_lut);
-  float* cvals = (float*)(smem + L.off_cv);
   const int pieces = p.a_pieces;
   const int acols = p.kpad / 4;
   const int nacc = p.nacc;
@@ -181,20 +248,33 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   if (threadIdx.x == 0) {
     mbar_init(bar(BAR_HFULL + 0), 1);
     mbar_init(bar(BAR_HFULL + 1), 1);
-    mbar_init(bar(BAR_HEMPTY + 0), 8);
-    mbar_init(bar(BAR_HEMPTY + 1), 8);
-    for (int s = 0; s < kBSlots; s++) {
-      mbar_init(bar(BAR_BFULL + s), 8);
+    mbar_init(bar(BAR_HEMPTY + 0), kGatherWarps);
+    mbar_init(bar(BAR_HEMPTY + 1), kGatherWarps);
+    for (int s = 0; s < p.nslots; s++) {
+      mbar_init(bar(BAR_BFULL + s), kGatherWarps);
       mbar_init(bar(BAR_BEMPTY + s), 1);
     }
     for (int a = 0; a < 2; a++) {
       mbar_init(bar(BAR_AFULL + a), 1);
       mbar_init(bar(BAR_AEMPTY + a), 4);
-      mbar_init(bar(BAR_CVFULL + a), 8);
+      mbar_init(bar(BAR_CVFULL + a), kGatherWarps);
     }
     mbar_init(bar(BAR_FINAL), 1);
-    *abort_flag = 0;
+    abort_flag[0] = 0;
+    abort_flag[1] = 0;
+    abort_flag[2] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
+    // the first tile's halo load overlaps the set-up below (when stage 0 is not needed for
+    // staging the A'' pieces)
+    if (p.early_tma && (int)blockIdx.x < p.num_tiles) {
+      const int tt = (int)blockIdx.x;
+      mbar_expect_tx(bar(BAR_HFULL), (uint32_t)p.box_h * (uint32_t)p.P * 4u);
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+              sbase),
+          "l"(&tmap_in), "r"((tt % p.tiles_x) * 128), "r"((tt / p.tiles_x) * 128), "r"(bar(BAR_HFULL))
+          : "memory");
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -202,6 +282,27 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   for (int i = threadIdx.x; i < p.kpad; i += blockDim.x) lut_s[i] = p.lut[i];
+  // A'' pieces and metadata: all threads copy them (16-byte loads) into a staging area that
+  // overlays halo stage 1 and the chunk slots (free until the main loop), rows padded so that
+  // the epilogue warps read them back without bank conflicts; then those warps store them to
+  // TMEM (lane = output row of the patch).
+  const int apitch = acols + 4;                       // words per staged A'' row
+  const int mpitch = p.kchunks | 1;                   // words per staged metadata row (odd)
+  const uint32_t stage_a = sbase + (p.early_tma ? L.halo_stride : 0u);  // staging area (shared address)
+  const uint32_t stage_m = stage_a + 4u * (uint32_t)(pieces * 128 * apitch);
+  {
+    const int q4 = acols / 4;  // uint4 per A'' row
+    const uint4* src = reinterpret_cast<const uint4*>(p.a_words);
+    for (int i = threadIdx.x; i < pieces * 128 * q4; i += blockDim.x) {
+      const uint4 v = src[i];
+      const int row = i / q4, c4 = i % q4;  // row = piece * 128 + lane
+      const uint32_t a = stage_a + 4u * (uint32_t)(row * apitch + 4 * c4);
+      asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                   : "memory");
+    }
+    for (int i = threadIdx.x; i < 128 * p.kchunks; i += blockDim.x)
+      sts_u32(stage_m + 4u * (uint32_t)((i / p.kchunks) * mpitch + i % p.kchunks), p.meta_words[i]);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -210,24 +311,29 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   const uint32_t meta_col = a_col + (uint32_t)(pieces * acols);
 
   if (warp >= 4 && warp < 8) {
-    // A'' pieces and the metadata into TMEM (lane = output row of the patch).
     const int q = warp - 4;
     const int row = 32 * q + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
     for (int pc = 0; pc < pieces; pc++) {
-      const uint32_t* src = p.a_words + ((size_t)pc * 128 + row) * acols;
+      const uint32_t ra = stage_a + 4u * (uint32_t)((pc * 128 + row) * apitch);
       for (int c = 0; c < acols; c += 8) {
-        uint32_t v0 = src[c], v1 = src[c + 1], v2 = src[c + 2], v3 = src[c + 3];
-        uint32_t v4 = src[c + 4], v5 = src[c + 5], v6 = src[c + 6], v7 = src[c + 7];
+        uint32_t v[8];
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                     : "r"(ra + 4u * (uint32_t)c));
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(ra + 4u * (uint32_t)(c + 4)));
         asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
                          lane_addr + a_col + (uint32_t)(pc * acols + c)),
-                     "r"(v0), "r"(v1), "r"(v2), "r"(v3), "r"(v4), "r"(v5), "r"(v6), "r"(v7));
+                     "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
       }
     }
     // chunk c's metadata column: an 8-column-aligned pair per two chunks, the instruction's
     // sparsity selector (0/1) picks the column inside the pair
     for (int c = 0; c < p.kchunks; c++) {
-      uint32_t v = p.meta_words[(size_t)row * p.kchunks + c];
+      uint32_t v;
+      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(stage_m + 4u * (uint32_t)(row * mpitch + c)));
       asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(
                        lane_addr + meta_col + 8u * (uint32_t)(c >> 1) + (uint32_t)(c & 1)),
                    "r"(v));
@@ -239,18 +345,21 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
 
   const int ntiles_cta = (p.num_tiles > (int)blockIdx.x) ? (p.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const bool tr = (blockIdx.x == 0) && g_trace_on;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       const uint32_t bytes = (uint32_t)p.box_h * (uint32_t)p.P * 4u;
-      int issued = 0;
-      for (int li = 0; li < ntiles_cta; li++) {
+      const int first = (p.early_tma && ntiles_cta > 0) ? 1 : 0;  // tile 0 was issued during set-up
+      int issued = first;
+      for (int li = first; li < ntiles_cta; li++) {
         const int stage = li & 1;
         if (li >= 2 && !mbar_wait(bar(BAR_HEMPTY + stage), ((li >> 1) - 1) & 1, wait_ns, abort_flag, p.status)) break;
         const int tt = (int)blockIdx.x + li * (int)gridDim.x;
         const int x0 = (tt % p.tiles_x) * 128, y0 = (tt / p.tiles_x) * 128;
         const uint32_t dst = sbase + (uint32_t)stage * L.halo_stride;
+        trace(tr, 0, li, 0);
         mbar_expect_tx(bar(BAR_HFULL + stage), bytes);
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -273,15 +382,20 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       idesc |= (p.fp16 ? 0u : 1u) << 10;     // B: FP16 (0) / BF16 (1)
       idesc |= (uint32_t)(128 >> 3) << 17;   // N = 128
       idesc |= (uint32_t)(128 >> 4) << 24;   // M = 128
-      uint32_t gchunk = 0;
+      uint32_t mslot = 0, mphase = 0;  // chunk ring position and wrap parity
       bool ok = true;
       for (int li = 0; li < ntiles_cta && ok; li++) {
         const int acc = li % nacc, use = li / nacc;
         if (use > 0 && !mbar_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
+        trace(tr, 1, li, 0);
         const uint32_t dcol = tmem + (uint32_t)(acc * 128);
-        for (int kc = 0; kc < p.kchunks; kc++, gchunk++) {
-          const uint32_t slot = gchunk % kBSlots, su = gchunk / kBSlots;
+        for (int kc = 0; kc < p.kchunks; kc++) {
+          const uint32_t slot = mslot, su = mphase;
+          if (++mslot == (uint32_t)p.nslots) {
+            mslot = 0;
+            mphase ^= 1u;
+          }
           if (!mbar_wait(bar(BAR_BFULL + slot), su & 1, wait_ns, abort_flag, p.status)) {
             ok = false;
             break;
@@ -305,6 +419,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         if (!ok) break;
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             bar(BAR_AFULL + acc)));
+        trace(tr, 1, li, 1);
       }
       // every MMA issued above completes before TMEM is released
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(BAR_FINAL)));
@@ -316,14 +431,22 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     const int rho = 32 * q + lane;
     const int ry = rho >> 4, rx = rho & 15;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+    const uint32_t cv_s = sbase + L.off_cv;
+    const int G = p.out_off;
+    const int64_t pitch8 = 8 * p.out_pitch;
     for (int li = 0; li < ntiles_cta; li++) {
       const int acc = li % nacc, use = li / nacc;
       if (!warp_wait(bar(BAR_AFULL + acc), use & 1, wait_ns, abort_flag, p.status)) break;
       if (!warp_wait(bar(BAR_CVFULL + acc), use & 1, wait_ns, abort_flag, p.status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
+      trace(tr && warp == 4 && lane == 0, 3, li, 0);
       const int tt = (int)blockIdx.x + li * (int)gridDim.x;
       const int x0 = (tt % p.tiles_x) * 128, y0 = (tt / p.tiles_x) * 128;
-      const float* cv = cvals + acc * 128;
+      // interior tiles: no bounds checks and no periodic images
+      const bool fast = (y0 + 128 <= p.H) && (x0 + 128 <= p.W) &&
+                        !(p.out_ghost && (y0 < G || y0 + 128 > p.H - G || x0 < G || x0 + 128 > p.W - G));
+      float* obase = p.out + (int64_t)(y0 + G + ry) * p.out_pitch + (x0 + G + rx);
+#pragma unroll 1
       for (int cg = 0; cg < 8; cg++) {
         uint32_t v[16];
         asm volatile(
@@ -331,27 +454,44 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(lane_addr + (uint32_t)(acc * 128 + cg * 16)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        float c[16];
+        const uint32_t ca = cv_s + (uint32_t)(acc * 128 + cg * 16) * 4u;
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-          const int n = cg * 16 + j;
-          const int px = (n >> 3) & 7, py = ((n >> 6) << 3) + (n & 7);
-          const int y = y0 + py * 8 + ry, x = x0 + px * 16 + rx;
-          const float c = cv[n];
-          const float val = fmaf(c, p.S_lo, fmaf(c, p.S_hi, __uint_as_float(v[j]) * p.wscale));
-          if (y < p.H && x < p.W) {
-            const int G = p.out_off;
-            p.out[(int64_t)(y + G) * p.out_pitch + (x + G)] = val;
-            if (p.out_ghost) {
-              const int ys[2] = {y < G ? y + p.H + G : -1, y >= p.H - G ? y - p.H + G : -1};
-              const int xs[2] = {x < G ? x + p.W + G : -1, x >= p.W - G ? x - p.W + G : -1};
-              for (int a = 0; a < 2; a++)
-                if (ys[a] >= 0) p.out[(int64_t)ys[a] * p.out_pitch + (x + G)] = val;
-              for (int b = 0; b < 2; b++)
-                if (xs[b] >= 0) p.out[(int64_t)(y + G) * p.out_pitch + xs[b]] = val;
-              for (int a = 0; a < 2; a++)
+        for (int k4 = 0; k4 < 4; k4++) {
+          const float4 c4 = lds_v4_f32(ca + 16u * k4);
+          c[4 * k4] = c4.x;
+          c[4 * k4 + 1] = c4.y;
+          c[4 * k4 + 2] = c4.z;
+          c[4 * k4 + 3] = c4.w;
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        // columns cg*16 .. +15 are patches (py, px) = (cg/4*8 + j%8, (2cg + j/8) % 8)
+        const int py0 = (cg >> 2) << 3, px0 = (2 * cg) & 7;
+        if (fast) {
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const float val = fmaf(c[j], p.S_lo, fmaf(c[j], p.S_hi, __uint_as_float(v[j]) * p.wscale));
+            obase[(int64_t)(py0 + (j & 7)) * pitch8 + (px0 + (j >> 3)) * 16] = val;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const int py = py0 + (j & 7), px = px0 + (j >> 3);
+            const int y = y0 + py * 8 + ry, x = x0 + px * 16 + rx;
+            const float val = fmaf(c[j], p.S_lo, fmaf(c[j], p.S_hi, __uint_as_float(v[j]) * p.wscale));
+            if (y < p.H && x < p.W) {
+              p.out[(int64_t)(y + G) * p.out_pitch + (x + G)] = val;
+              if (p.out_ghost) {
+                const int ys[2] = {y < G ? y + p.H + G : -1, y >= p.H - G ? y - p.H + G : -1};
+                const int xs[2] = {x < G ? x + p.W + G : -1, x >= p.W - G ? x - p.W + G : -1};
+                for (int a = 0; a < 2; a++)
+                  if (ys[a] >= 0) p.out[(int64_t)ys[a] * p.out_pitch + (x + G)] = val;
                 for (int b = 0; b < 2; b++)
-                  if (ys[a] >= 0 && xs[b] >= 0) p.out[(int64_t)ys[a] * p.out_pitch + xs[b]] = val;
+                  if (xs[b] >= 0) p.out[(int64_t)(y + G) * p.out_pitch + xs[b]] = val;
+                for (int a = 0; a < 2; a++)
+                  for (int b = 0; b < 2; b++)
+                    if (ys[a] >= 0 && xs[b] >= 0) p.out[(int64_t)ys[a] * p.out_pitch + xs[b]] = val;
+              }
             }
           }
         }
@@ -359,67 +499,97 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(BAR_AEMPTY + acc));
+      trace(tr && warp == 4 && lane == 0, 3, li, 1);
     }
-  } else if (warp >= 8) {
+  } else if (warp >= kGatherWarp0) {
     // ---------------- B'' gather ----------------
-    const int gw = warp - 8;
+    // Lane (h, pl) handles pair pl (K rows 2pl, 2pl+1) of each chunk for patch n0 + 8h of each
+    // of its patch pairs: the two patches are one x-step apart (their tile offsets differ by 16
+    // words, so the half-warps use disjoint banks) and land in different 8-patch groups (their
+    // B'' offsets differ by SBO = 16 words mod 32).  All loads of a chunk are issued before
+    // any of them is used, and before the wait for the chunk's slot.
+    const int gw = warp - kGatherWarp0;
     const int h = lane >> 4, pl = lane & 15;
     const uint32_t pairoff = (uint32_t)((pl >> 2) * kLBO + (pl & 3) * 4);
     const int P = p.P, G = p.G;
-    uint32_t gchunk = 0;
-    int base_i[8], n_i[8];
-    uint32_t soff_i[8];
+    uint32_t slot = 0, sphase = 0, used = 0;  // chunk ring position, wrap parity, chunks written
+    int base_i[kItems], n_i[kItems];
+    uint32_t soff_i[kItems];
 #pragma unroll
-    for (int i = 0; i < 8; i++) {
-      const int pp = gw + 8 * i;
+    for (int i = 0; i < kItems; i++) {
+      const int pp = gw + kGatherWarps * i;
       const int n = (pp >> 3) * 16 + (pp & 7) + 8 * h;
       const int px = (n >> 3) & 7, py = ((n >> 6) << 3) + (n & 7);
       n_i[i] = n;
-      base_i[i] = py * 8 * P + px * 16;
+      base_i[i] = 4 * (py * 8 * P + px * 16);
       soff_i[i] = (uint32_t)((n >> 3) * kSBO + (n & 7) * 16) + pairoff;
     }
+    const uint32_t lut_sa = sbase + L.off_lut + 8u * (uint32_t)pl;
     for (int li = 0; li < ntiles_cta; li++) {
       const int stage = li & 1, acc = li % nacc, use = li / nacc;
       if (!warp_wait(bar(BAR_HFULL + stage), (li >> 1) & 1, wait_ns, abort_flag, p.status)) break;
-      const float* tile = (const float*)(smem + (size_t)stage * L.halo_stride);
-      float c_i[8];
+      trace(tr && gw == 0 && lane == 0, 2, li, 0);
+      const uint32_t tile_s = sbase + (uint32_t)stage * L.halo_stride;
+      uint32_t ba[kItems];
+      float c_i[kItems];
 #pragma unroll
-      for (int i = 0; i < 8; i++) c_i[i] = tile[base_i[i] + G * P + G];
+      for (int i = 0; i < kItems; i++) {
+        ba[i] = tile_s + (uint32_t)base_i[i];
+        c_i[i] = lds_f32(ba[i] + 4u * (uint32_t)(G * P + G));
+      }
       if (use > 0 && !warp_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
       if (pl == 0) {
 #pragma unroll
-        for (int i = 0; i < 8; i++) cvals[acc * 128 + n_i[i]] = c_i[i];
+        for (int i = 0; i < kItems; i++) sts_f32(sbase + L.off_cv + 4u * (uint32_t)(acc * 128 + n_i[i]), c_i[i]);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(BAR_CVFULL + acc));
       bool ok = true;
-      for (int kc = 0; kc < p.kchunks; kc++, gchunk++) {
-        const uint32_t slot = gchunk % kBSlots, su = gchunk / kBSlots;
-        if (su > 0 && !warp_wait(bar(BAR_BEMPTY + slot), (su - 1) & 1, wait_ns, abort_flag, p.status)) {
+      const bool trc = tr && gw == 0 && lane == 0 && li == 1;
+      for (int kc = 0; kc < p.kchunks; kc++) {
+        trace_chunk(trc, kc, 0);
+        const int2 lab = lds_v2_s32(lut_sa + 128u * (uint32_t)kc);
+        const uint32_t la = 4u * (uint32_t)lab.x, lb = 4u * (uint32_t)lab.y;
+        float va[kItems], vb[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+          va[i] = lds_f32(ba[i] + la);
+          vb[i] = lds_f32(ba[i] + lb);
+        }
+        trace_chunk(trc, kc, 1);
+        if (used >= (uint32_t)p.nslots &&
+            !warp_wait(bar(BAR_BEMPTY + slot), sphase ^ 1u, wait_ns, abort_flag, p.status)) {
           ok = false;
           break;
         }
-        const int la = lut_s[kc * 32 + 2 * pl], lb = lut_s[kc * 32 + 2 * pl + 1];
-        uint8_t* bs = smem + L.off_b + slot * L.slot_bytes;
+        trace_chunk(trc, kc, 2);
+        const uint32_t bs = sbase + L.off_b + slot * L.slot_bytes;
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-          const float da = tile[base_i[i] + la] - c_i[i];
-          const float db = tile[base_i[i] + lb] - c_i[i];
-          const uint32_t hi = pack2(da, db, p.fp16);
-          *(uint32_t*)(bs + soff_i[i]) = hi;
-          if (p.b_pieces > 1) {
+        for (int i = 0; i < kItems; i++) {
+          const float da = va[i] - c_i[i];
+          const float db = vb[i] - c_i[i];
+          const uint32_t hi = pack2(da, db, FP16);
+          sts_u32(bs + soff_i[i], hi);
+          if (SPLIT) {
             float ha, hb;
-            unpack2(hi, p.fp16, ha, hb);
-            *(uint32_t*)(bs + kPieceBytes + soff_i[i]) = pack2(da - ha, db - hb, p.fp16);
+            unpack2(hi, FP16, ha, hb);
+            sts_u32(bs + kPieceBytes + soff_i[i], pack2(da - ha, db - hb, FP16));
           }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(BAR_BFULL + slot));
+        used++;
+        if (++slot == (uint32_t)p.nslots) {
+          slot = 0;
+          sphase ^= 1u;
+        }
+        trace_chunk(trc, kc, 3);
       }
       if (!ok) break;
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(BAR_HEMPTY + stage));
+      trace(tr && gw == 0 && lane == 0, 2, li, 1);
     }
   }
 
@@ -434,13 +604,67 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 
 size_t sweep2d_smem_bytes(const Sweep2DParams& p) { return (size_t)SmemLayout(p).total + 1024; }
 
-cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p, int num_sms, cudaStream_t stream) {
+cudaError_t sweep_trace_enable(int on) {
+  if (!SPST_TRACE) return cudaErrorNotSupported;
+  cudaError_t e = cudaMemcpyToSymbol(g_trace_on, &on, sizeof(int));
+  if (e != cudaSuccess) return e;
+  static const unsigned long long zeros[4 * kTraceTiles * 2] = {0};
+  e = cudaMemcpyToSymbol(g_trace_chunks, zeros, 64 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(g_trace, zeros, sizeof(zeros));
+}
+
+cudaError_t sweep_trace_read(unsigned long long* out, int n) {
+  const int n1 = 4 * kTraceTiles * 2;
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_trace, (size_t)(n < n1 ? n : n1) * sizeof(unsigned long long));
+  if (e != cudaSuccess || n <= n1) return e;
+  const int n2 = (n - n1 < 64) ? n - n1 : 64;
+  return cudaMemcpyFromSymbol(out + n1, g_trace_chunks, (size_t)n2 * sizeof(unsigned long long));
+}
+
+#ifndef SPST_SLOT_CAP
+#define SPST_SLOT_CAP kMaxBSlots
+#endif
+// Bytes of the A'' / metadata staging area used during set-up.
+static size_t staging_bytes(const Sweep2DParams& p) {
+  const int acols = p.kpad / 4;
+  return 4u * ((size_t)p.a_pieces * 128 * (acols + 4) + (size_t)128 * (p.kchunks | 1));
+}
+
+int sweep2d_max_slots(const Sweep2DParams& p) {
+  Sweep2DParams q = p;
+  for (int n = SPST_SLOT_CAP; n >= 1; n--) {
+    q.nslots = n;
+    if (sweep2d_smem_bytes(q) <= 232448) return n;
+  }
+  return 0;
+}
+
+bool sweep2d_fits(const Sweep2DParams& p_in) {
+  Sweep2DParams p = p_in;
+  p.nslots = sweep2d_max_slots(p);
+  if (p.nslots < 2) return false;
+  return staging_bytes(p) <= (size_t)SmemLayout(p).off_lut;
+}
+
+cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p_in, int num_sms, cudaStream_t stream) {
+  Sweep2DParams p = p_in;
+  p.nslots = sweep2d_max_slots(p);
+  if (p.nslots < 2) return cudaErrorInvalidConfiguration;
+  {
+    const SmemLayout L(p);
+    const size_t need = staging_bytes(p);
+    p.early_tma = (need <= (size_t)(L.off_lut - L.halo_stride)) ? 1 : 0;
+    if (need > (size_t)L.off_lut) return cudaErrorInvalidConfiguration;
+  }
   const size_t smem = sweep2d_smem_bytes(p);
-  cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1> : sweep2d_kernel<1, 0>)
+                     : (p.b_pieces > 1 ? sweep2d_kernel<0, 1> : sweep2d_kernel<0, 0>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
   if (grid < 1) return cudaSuccess;
-  sweep2d_kernel<<<grid, kSweepThreads, smem, stream>>>(tmap_in, p);
+  kern<<<grid, kSweepThreads, smem, stream>>>(tmap_in, p);
   return cudaGetLastError();
 }
 
