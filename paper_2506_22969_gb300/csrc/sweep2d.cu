@@ -442,9 +442,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       trace(tr && warp == 4 && lane == 0, 3, li, 0);
       const int tt = (int)blockIdx.x + li * (int)gridDim.x;
       const int x0 = (tt % p.tiles_x) * 128, y0 = (tt / p.tiles_x) * 128;
-      // interior tiles: no bounds checks and no periodic images
-      const bool fast = (y0 + 128 <= p.H) && (x0 + 128 <= p.W) &&
-                        !(p.out_ghost && (y0 < G || y0 + 128 > p.H - G || x0 < G || x0 + 128 > p.W - G));
+      // full tiles store without bounds checks; tiles that touch the ghost band of a periodic
+      // padded output also write the images of their band outputs
+      const bool full = (y0 + 128 <= p.H) && (x0 + 128 <= p.W);
+      const bool ghost = p.out_ghost && (y0 < G || y0 + 128 > p.H - G || x0 < G || x0 + 128 > p.W - G);
       float* obase = p.out + (int64_t)(y0 + G + ry) * p.out_pitch + (x0 + G + rx);
 #pragma unroll 1
       for (int cg = 0; cg < 8; cg++) {
@@ -467,32 +468,30 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         // columns cg*16 .. +15 are patches (py, px) = (cg/4*8 + j%8, (2cg + j/8) % 8)
         const int py0 = (cg >> 2) << 3, px0 = (2 * cg) & 7;
-        if (fast) {
+        float val[16];
 #pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const float val = fmaf(c[j], p.S_lo, fmaf(c[j], p.S_hi, __uint_as_float(v[j]) * p.wscale));
-            obase[(int64_t)(py0 + (j & 7)) * pitch8 + (px0 + (j >> 3)) * 16] = val;
-          }
+        for (int j = 0; j < 16; j++) val[j] = fmaf(c[j], p.S_lo, fmaf(c[j], p.S_hi, __uint_as_float(v[j]) * p.wscale));
+        if (full) {
+#pragma unroll
+          for (int j = 0; j < 16; j++) obase[(int64_t)(py0 + (j & 7)) * pitch8 + (px0 + (j >> 3)) * 16] = val[j];
         } else {
 #pragma unroll
           for (int j = 0; j < 16; j++) {
-            const int py = py0 + (j & 7), px = px0 + (j >> 3);
-            const int y = y0 + py * 8 + ry, x = x0 + px * 16 + rx;
-            const float val = fmaf(c[j], p.S_lo, fmaf(c[j], p.S_hi, __uint_as_float(v[j]) * p.wscale));
-            if (y < p.H && x < p.W) {
-              p.out[(int64_t)(y + G) * p.out_pitch + (x + G)] = val;
-              if (p.out_ghost) {
-                const int ys[2] = {y < G ? y + p.H + G : -1, y >= p.H - G ? y - p.H + G : -1};
-                const int xs[2] = {x < G ? x + p.W + G : -1, x >= p.W - G ? x - p.W + G : -1};
-                for (int a = 0; a < 2; a++)
-                  if (ys[a] >= 0) p.out[(int64_t)ys[a] * p.out_pitch + (x + G)] = val;
-                for (int b = 0; b < 2; b++)
-                  if (xs[b] >= 0) p.out[(int64_t)(y + G) * p.out_pitch + xs[b]] = val;
-                for (int a = 0; a < 2; a++)
-                  for (int b = 0; b < 2; b++)
-                    if (ys[a] >= 0 && xs[b] >= 0) p.out[(int64_t)ys[a] * p.out_pitch + xs[b]] = val;
-              }
-            }
+            const int y = y0 + (py0 + (j & 7)) * 8 + ry, x = x0 + (px0 + (j >> 3)) * 16 + rx;
+            if (y < p.H && x < p.W) obase[(int64_t)(py0 + (j & 7)) * pitch8 + (px0 + (j >> 3)) * 16] = val[j];
+          }
+        }
+        if (ghost) {
+          for (int j = 0; j < 16; j++) {
+            const int y = y0 + (py0 + (j & 7)) * 8 + ry, x = x0 + (px0 + (j >> 3)) * 16 + rx;
+            if (y >= p.H || x >= p.W) continue;
+            const bool by = (y < G) || (y >= p.H - G), bx = (x < G) || (x >= p.W - G);
+            if (!by && !bx) continue;
+            const int yi = y < G ? y + p.H + G : (y >= p.H - G ? y - p.H + G : -1);
+            const int xi = x < G ? x + p.W + G : (x >= p.W - G ? x - p.W + G : -1);
+            if (yi >= 0) p.out[(int64_t)yi * p.out_pitch + (x + G)] = val[j];
+            if (xi >= 0) p.out[(int64_t)(y + G) * p.out_pitch + xi] = val[j];
+            if (yi >= 0 && xi >= 0) p.out[(int64_t)yi * p.out_pitch + xi] = val[j];
           }
         }
       }
