@@ -222,7 +222,7 @@ def trace_case():
             torch.cuda.synchronize()
             binding.trace(True)
             c_ms, s_ms, n = plan.run_profiled(x, y, t)
-            tr, ch = binding.trace_read()
+            tr, ch, pub = binding.trace_read()
             binding.trace(False)
             t0 = int(np.min(tr[tr > 0])) if np.any(tr > 0) else 0
             ntile = int(np.sum(tr[1, :, 0] > 0))
@@ -234,11 +234,14 @@ def trace_case():
                                                      if tr[r, li, 0] else f"{names[r]}    -   ")
                                for r in range(4))
                 print(f"  tile {li}: {row}")
-            c0 = ch[0, 0]
+            c0 = ch[0, 0, 0]
             for kc in range(16):
-                if ch[kc, 0]:
-                    print(f"  tile 1 chunk {kc}: start {ch[kc, 0] - c0:6d} loaded {ch[kc, 1] - c0:6d} "
-                          f"slot-free {ch[kc, 2] - c0:6d} published {ch[kc, 3] - c0:6d} (cycles)")
+                if ch[0, kc, 0]:
+                    g = " | ".join(f"w{s}: start {ch[s, kc, 0] - c0:6d} loaded {ch[s, kc, 1] - c0:6d} "
+                                   f"free {ch[s, kc, 2] - c0:6d} pub {ch[s, kc, 3] - c0:6d}" for s in (0, 1))
+                    print(f"  tile 1 chunk {kc:2d}: {g} | mma ready {ch[2, kc, 0] - c0:6d} "
+                          f"issued {ch[2, kc, 1] - c0:6d} (cycles)")
+                    print("      publish by gather warp: " + " ".join(f"{pub[w, kc] - c0:6d}" for w in range(16)))
 
 
 def main():

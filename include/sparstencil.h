@@ -105,10 +105,11 @@ sparstencil_status sparstencil_run(sparstencil_plan_t plan, const float* in, flo
 sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in_host, float* out_host,
                                         int64_t timesteps, cudaStream_t stream);
 
-/* Same as sparstencil_run, but records CUDA events around every kernel it launches and
- * synchronises `stream` before returning:
+/* Same as sparstencil_run, but records CUDA events before and after the copy into the
+ * padded grid and after the last sweep, and synchronises `stream` before returning:
  *   copy_in_ms:  device time of the copy into the padded grid (may be NULL)
- *   sweeps_ms:   total device time of the sweep kernels (may be NULL)
+ *   sweeps_ms:   device time from the end of that copy to the end of the last sweep, gaps
+ *                between consecutive sweeps included (may be NULL)
  *   num_sweeps:  number of sweep kernels launched (may be NULL)
  * Used by the benchmark to report the sweep kernel's own bandwidth. */
 sparstencil_status sparstencil_run_profiled(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
@@ -202,9 +203,11 @@ sparstencil_status sparstencil_set_wait_limit_ns(uint64_t ns);
 sparstencil_status sparstencil_trace(int enable);
 
 /* Copies up to n trace entries to host memory; synchronous.  Entries 0..511: layout
- * [role][tile][start, end] (4 x 64 x 2, nanoseconds); entries 512..575: clock64 stamps of
- * the first gather warp's K chunks of CTA 0's second tile, [chunk < 16][chunk start, halo
- * values loaded, chunk slot free, chunk published]. */
+ * [role][tile][start, end] (4 x 64 x 2, nanoseconds); entries 512..703: clock64 stamps of
+ * the K chunks of CTA 0's second tile, [source][chunk < 16][4]: sources 0 and 1 the first and
+ * the last B'' gather warp (chunk start, halo values loaded, chunk slot free, chunk
+ * published), source 2 the MMA issuer (chunk complete in shared memory, MMAs issued);
+ * entries 704..959: [gather warp < 16][chunk < 16] publish stamps of the same tile. */
 sparstencil_status sparstencil_trace_read(uint64_t* out, int n);
 
 /* Thread-local description of the last failure in this thread ("" if none). */

@@ -15,10 +15,11 @@ Contents
     graph (Def. 1), Algorithm 1 (hierarchical two-level matching), a brute-force solver
     for Problem 1, the 2:4 rule (Eq. 2) and the dense stencil matrix.
 
-Readings of the paper that this oracle takes where the text is silent are listed in
-DESIGN.md ("Readings of the paper").  Every function here is pinned by a ``-m "not
-gpu"`` test against something other than itself (closed forms, invariants, brute force,
-textbook special cases).
+Where the paper is silent this oracle takes these readings: the stencil is a correlation
+(offsets not flipped); a Dirichlet boundary is a zero halo re-imposed after every step, a
+periodic one wraps indices; T steps are taken one by one in FP64 with no intermediate
+rounding.  Every function here is pinned by a ``-m "not gpu"`` test against something
+other than itself (closed forms, invariants, brute force, textbook special cases).
 """
 from __future__ import annotations
 

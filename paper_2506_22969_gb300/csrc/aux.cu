@@ -43,18 +43,24 @@ __global__ void pad_copy2d_kernel(const float* __restrict__ in, float* __restric
 // tile in shared memory (coalesced loads, boundary rule applied on load) and each thread
 // computes outputs with FP32 FMAs in fixed offset order.  One time step per launch.
 // ---------------------------------------------------------------------------------------
-constexpr int DTX = 64, DTY = 16;
+// 2D: a CTA covers 128 x 32 outputs with 256 threads; thread (column cx, half ch) computes
+// the 16 outputs of column cx in rows 16ch .. 16ch+15.  It walks the 16 + 2R input rows of
+// its strip once, loading each row's 2R+1 horizontal neighbours from shared memory, and adds
+// each loaded value into every output row that uses it, in the fixed offset order (dy, dx)
+// lexicographic per output (weights live in registers).
+constexpr int DTX = 128, DTY = 32, DSTRIP = 16;
 
-__global__ void direct2d_kernel(const __grid_constant__ DirectParams p, const float* __restrict__ in,
-                                float* __restrict__ out) {
+template <int R>
+__global__ void __launch_bounds__(256) direct2d_kernel(const __grid_constant__ DirectParams p,
+                                                       const float* __restrict__ in, float* __restrict__ out) {
   extern __shared__ float tile[];
-  const int r = p.radius;
-  const int tw = DTX + 2 * r, th = DTY + 2 * r;
+  constexpr int K = 2 * R + 1;
+  constexpr int TW = DTX + 2 * R, TH = DTY + 2 * R;
   const int64_t H = p.H, W = p.W;
   const int64_t x0 = (int64_t)blockIdx.x * DTX, y0 = (int64_t)blockIdx.y * DTY;
-  for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
-    const int ty = i / tw, tx = i % tw;
-    int64_t y = y0 + ty - r, x = x0 + tx - r;
+  for (int i = threadIdx.x; i < TW * TH; i += blockDim.x) {
+    const int ty = i / TW, tx = i % TW;
+    int64_t y = y0 + ty - R, x = x0 + tx - R;
     float v = 0.f;
     if (p.periodic) {
       y = y < 0 ? y + H : (y >= H ? y - H : y);
@@ -65,15 +71,30 @@ __global__ void direct2d_kernel(const __grid_constant__ DirectParams p, const fl
     }
     tile[i] = v;
   }
+  float w[K][K];
+#pragma unroll
+  for (int a = 0; a < K; a++)
+#pragma unroll
+    for (int b = 0; b < K; b++) w[a][b] = p.wdense[a * K + b];
   __syncthreads();
-  const int npts = p.npts;
-  for (int i = threadIdx.x; i < DTX * DTY; i += blockDim.x) {
-    const int ly = i / DTX, lx = i % DTX;
-    const int64_t y = y0 + ly, x = x0 + lx;
-    if (y >= H || x >= W) continue;
-    float acc = 0.f;
-    for (int q = 0; q < npts; q++) acc = fmaf(p.w[q], tile[(ly + r + p.off[q][1]) * tw + (lx + r + p.off[q][2])], acc);
-    out[y * W + x] = acc;
+  const int cx = threadIdx.x % DTX, ch = threadIdx.x / DTX;
+  float acc[DSTRIP];
+#pragma unroll
+  for (int k = 0; k < DSTRIP; k++) acc[k] = 0.f;
+  // input row r (strip-relative, 0 .. DSTRIP+2R-1) feeds output k through weight row dy = r - k
+#pragma unroll
+  for (int dy = 0; dy < K; dy++) {
+#pragma unroll
+    for (int k = 0; k < DSTRIP; k++) {
+      const float* row = tile + (ch * DSTRIP + k + dy) * TW + cx;
+#pragma unroll
+      for (int dx = 0; dx < K; dx++) acc[k] = fmaf(w[dy][dx], row[dx], acc[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < DSTRIP; k++) {
+    const int64_t y = y0 + ch * DSTRIP + k, x = x0 + cx;
+    if (y < H && x < W) out[y * W + x] = acc[k];
   }
 }
 
@@ -142,6 +163,74 @@ __global__ void norms_kernel(const float* __restrict__ x, const float* __restric
   }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Dirichlet band of a fused sweep.  The composed t-step kernel is exact only at points at
+// least (t-1)r from every edge, because the zero boundary is imposed once per sweep instead
+// of after every step.  Each CTA recomputes a rectangle of the band (the top and bottom
+// rows [0, bw) and [H-bw, H), then the left and right columns of the rows in between) from
+// the sweep's input: it stages the rectangle widened by t*r on each side (zeros outside the
+// grid), takes t single steps in shared memory with the zero boundary re-imposed after each
+// one, and writes the rectangle.  Window cells whose stencil leaves the window become
+// invalid; that error moves r cells inward per step, so after t steps it has not reached
+// the rectangle.
+// ---------------------------------------------------------------------------------------
+__global__ void band2d_kernel(const BandParams p) {
+  extern __shared__ float bsm[];
+  const int H = p.H, W = p.W, bw = p.bw, seg = p.seg, r = p.radius;
+  const int top_h = bw < H ? bw : H;
+  const int bot_y0 = (H - bw > top_h) ? H - bw : top_h;
+  const int mid_h = H - 2 * bw;
+  const int left_w = bw < W ? bw : W;
+  const int right_x0 = (W - bw > left_w) ? W - bw : left_w;
+  int b = (int)blockIdx.x, ty0, ty1, tx0, tx1;
+  if (b < p.nx) {
+    ty0 = 0, ty1 = top_h, tx0 = b * seg, tx1 = min(W, tx0 + seg);
+  } else if ((b -= p.nx) < p.nx) {
+    ty0 = bot_y0, ty1 = H, tx0 = b * seg, tx1 = min(W, tx0 + seg);
+  } else if ((b -= p.nx) < p.ny) {
+    ty0 = bw + b * seg, ty1 = min(bw + mid_h, ty0 + seg), tx0 = 0, tx1 = left_w;
+  } else {
+    b -= p.ny;
+    ty0 = bw + b * seg, ty1 = min(bw + mid_h, ty0 + seg), tx0 = right_x0, tx1 = W;
+  }
+  if (ty0 >= ty1 || tx0 >= tx1) return;
+  const int M = p.t * r;
+  const int wy0 = ty0 - M, wx0 = tx0 - M;
+  const int WH = ty1 - ty0 + 2 * M, WW = tx1 - tx0 + 2 * M;
+  const int n = WH * WW;
+  float* a = bsm;
+  float* c = bsm + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int y = wy0 + i / WW, x = wx0 + i % WW;
+    a[i] = (y >= 0 && y < H && x >= 0 && x < W) ? p.src[(int64_t)(y + p.src_off) * p.src_pitch + x + p.src_off] : 0.f;
+  }
+  __syncthreads();
+  const int side = 2 * r + 1;
+  for (int s = 0; s < p.t; s++) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int yy = i / WW, xx = i % WW;
+      const int y = wy0 + yy, x = wx0 + xx;
+      float v = 0.f;
+      if (y >= 0 && y < H && x >= 0 && x < W && yy >= r && yy < WH - r && xx >= r && xx < WW - r) {
+        const float* q = a + (yy - r) * WW + (xx - r);
+        for (int dy = 0; dy < side; dy++)
+          for (int dx = 0; dx < side; dx++) v = fmaf(p.w[dy * side + dx], q[dy * WW + dx], v);
+      }
+      c[i] = v;
+    }
+    __syncthreads();
+    float* tmp = a;
+    a = c;
+    c = tmp;
+  }
+  const int th = ty1 - ty0, tw = tx1 - tx0;
+  for (int i = threadIdx.x; i < th * tw; i += blockDim.x) {
+    const int y = ty0 + i / tw, x = tx0 + i % tw;
+    p.dst[(int64_t)(y + p.dst_off) * p.dst_pitch + x + p.dst_off] = a[(y - wy0) * WW + (x - wx0)];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_pad_copy2d(const float* in, float* padded, int H, int W, int G, int64_t Wp, int periodic,
@@ -153,25 +242,60 @@ cudaError_t launch_pad_copy2d(const float* in, float* padded, int H, int W, int 
   return cudaGetLastError();
 }
 
+template <int R>
+static cudaError_t launch_direct2d(const DirectParams& p, const float* in, float* out, cudaStream_t stream) {
+  dim3 grid((unsigned)((p.W + DTX - 1) / DTX), (unsigned)((p.H + DTY - 1) / DTY));
+  const size_t smem = (size_t)(DTX + 2 * R) * (DTY + 2 * R) * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(direct2d_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  direct2d_kernel<R><<<grid, 256, smem, stream>>>(p, in, out);
+  return cudaGetLastError();
+}
+
+size_t band2d_smem_bytes(int bw, int t, int radius, int seg) {
+  const size_t M = (size_t)t * radius;
+  const size_t a = ((size_t)bw + 2 * M) * ((size_t)seg + 2 * M);
+  return 2 * a * sizeof(float);
+}
+
+cudaError_t launch_band2d(BandParams p, cudaStream_t stream) {
+  if (p.t < 2 || p.bw <= 0) return cudaSuccess;
+  // largest segment (128 down to 8) whose two window buffers fit in shared memory
+  int seg = 128;
+  while (seg > 8 && band2d_smem_bytes(p.bw, p.t, p.radius, seg) > 200 * 1024) seg /= 2;
+  const size_t smem = band2d_smem_bytes(p.bw, p.t, p.radius, seg);
+  if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+  p.seg = seg;
+  p.nx = (p.W + seg - 1) / seg;
+  const int mid = p.H - 2 * p.bw;
+  p.ny = mid > 0 ? (mid + seg - 1) / seg : 0;
+  const int blocks = 2 * p.nx + 2 * p.ny;
+  cudaError_t e = cudaFuncSetAttribute(band2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  band2d_kernel<<<blocks, 256, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* out, cudaStream_t stream) {
   const int r = p.radius;
   if (p.ndim == 2) {
-    dim3 grid((unsigned)((p.W + DTX - 1) / DTX), (unsigned)((p.H + DTY - 1) / DTY));
-    size_t smem = (size_t)(DTX + 2 * r) * (DTY + 2 * r) * sizeof(float);
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(direct2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
+    switch (r) {
+      case 1: return launch_direct2d<1>(p, in, out, stream);
+      case 2: return launch_direct2d<2>(p, in, out, stream);
+      case 3: return launch_direct2d<3>(p, in, out, stream);
+      case 4: return launch_direct2d<4>(p, in, out, stream);
+      default: return cudaErrorInvalidValue;
     }
-    direct2d_kernel<<<grid, 256, smem, stream>>>(p, in, out);
-  } else {
-    dim3 grid((unsigned)((p.W + D3X - 1) / D3X), (unsigned)((p.H + D3Y - 1) / D3Y), (unsigned)((p.D + D3Z - 1) / D3Z));
-    size_t smem = (size_t)(D3X + 2 * r) * (D3Y + 2 * r) * (D3Z + 2 * r) * sizeof(float);
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(direct3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    direct3d_kernel<<<grid, 256, smem, stream>>>(p, in, out);
   }
+  dim3 grid((unsigned)((p.W + D3X - 1) / D3X), (unsigned)((p.H + D3Y - 1) / D3Y), (unsigned)((p.D + D3Z - 1) / D3Z));
+  size_t smem = (size_t)(D3X + 2 * r) * (D3Y + 2 * r) * (D3Z + 2 * r) * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(direct3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  direct3d_kernel<<<grid, 256, smem, stream>>>(p, in, out);
   return cudaGetLastError();
 }
 

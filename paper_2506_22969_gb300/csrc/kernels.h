@@ -8,7 +8,12 @@
 
 namespace spst {
 
-constexpr int kSweepThreads = 768;   // 24 warps: TMA, MMA, 2 spare, 4 epilogue, 16 gather
+#ifndef SPST_EPI_WARPS
+#define SPST_EPI_WARPS 8
+#endif
+constexpr int kEpiWarps = SPST_EPI_WARPS;  // epilogue warps (4 or 8)
+// warps: TMA, MMA, 2 spare, kEpiWarps epilogue, 16 gather
+constexpr int kSweepThreads = (4 + kEpiWarps + 16) * 32;
 constexpr int kHaloStages = 2;
 constexpr int kMaxBSlots = 8;        // ring of B'' K chunks (the launcher fills the shared memory left)
 constexpr int kPieceBytes = 16 * 576;  // one K-chunk (32 x 128, 16-bit) of B' in the padded K-major layout
@@ -68,11 +73,28 @@ struct DirectParams {
   int radius;
   int periodic;
   int npts;
-  int off[343][3];      // offsets (z, y, x)
-  float w[343];
+  int off[343][3];      // offsets (z, y, x) of the nonzero weights
+  float w[343];         // their weights (FP32 FMAs in this order)
+  float wdense[81];     // 2D: the dense (2r+1)^2 cube (zeros included), r <= 4
 };
 // One FP32 CUDA-core step in -> out.
 cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* out, cudaStream_t stream);
+
+// Dirichlet band of a fused sweep of depth t >= 2: exact step-by-step FP32 values in the
+// frame of width bw = (t-1)*radius inside the grid edges, from the sweep's input.
+struct BandParams {
+  const float* src;       // the sweep's input grid
+  int64_t src_pitch;      // floats per row of src
+  int src_off;            // ghost width of src (cell (0,0) at src[src_off * src_pitch + src_off])
+  float* dst;             // the sweep's output grid (band cells overwritten)
+  int64_t dst_pitch;
+  int dst_off;
+  int H, W;
+  int radius, t, bw;
+  int seg, nx, ny;        // set by launch_band2d
+  float w[81];            // single-step weights, dense (2r+1)^2 [dy][dx], r <= 4
+};
+cudaError_t launch_band2d(BandParams p, cudaStream_t stream);
 
 // FP64 norms of x against ref (see sparstencil_error_norms); acc: 4 doubles of device memory.
 cudaError_t launch_error_norms(const float* x, const float* ref, int64_t n, double* acc, cudaStream_t stream);

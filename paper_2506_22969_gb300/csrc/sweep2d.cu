@@ -70,14 +70,31 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded single-thread wait: returns false on timeout, or when abort_flag (may be null) is
-// set by another role.  A timeout sets abort_flag and records SPST_ERR_TIMEOUT.
+// Non-suspending probe of the phase (mbarrier.test_wait).
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// try_wait may suspend the thread for several microseconds before it reports an incomplete
+// phase, so a wait limit below this is enforced with test_wait polls instead (the limit then
+// holds to within a poll, at the cost of spinning).
+constexpr uint64_t kSuspendingPollMinNs = 100000;
+__device__ __forceinline__ bool mbar_poll(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  return limit_ns < kSuspendingPollMinNs ? mbar_test(bar, parity) : mbar_try(bar, parity);
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns, volatile int* abort_flag,
                                           int* status) {
-  if (mbar_try(bar, parity)) return true;
+  if (mbar_poll(bar, parity, limit_ns)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_poll(bar, parity, limit_ns)) return true;
     if (abort_flag && *abort_flag) return false;
     if (gtimer() - t0 > limit_ns) {
       if (abort_flag) *abort_flag = 1;
@@ -96,10 +113,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns, volatile int* abort_flag,
                                           int* status) {
 #if SPST_POLL_ALL_LANES
+  // the clock is read only once the first poll has failed: a wait that is already satisfied
+  // costs one poll and one vote
+  if (__all_sync(0xffffffffu, mbar_test(bar, parity))) return true;
   const uint64_t t0 = gtimer();
   const int lane = threadIdx.x & 31;
   while (true) {
-    const bool d = mbar_try(bar, parity);
+    const bool d = mbar_poll(bar, parity, limit_ns);
     if (__all_sync(0xffffffffu, d)) return true;
     int give_up = 0;
     if (lane == 0) give_up = (*abort_flag) ? 1 : ((gtimer() - t0 > limit_ns) ? 2 : 0);
@@ -128,6 +148,54 @@ __device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo, uin
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; no swizzle, base offset 0
   return d;
+}
+
+// tcgen05.commit by one elected lane of a converged warp: the barrier gets one arrival when
+// every tcgen05 operation the issuing thread started before it has completed.
+__device__ __forceinline__ void commit_elected(uint32_t bar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(bar)
+      : "memory");
+}
+
+// One K chunk's MMAs (1 to 4 terms: A piece x B piece, all into the accumulator at d) and
+// the commit that frees the chunk's B'' slot, issued by one elected lane of a converged warp
+// in a single block.  en: accumulate onto d for the first term (0 for the tile's first chunk).
+#define SPST_MMA_SP(A, B, P) " @e tcgen05.mma.sp.cta_group::1.kind::f16 [%0], [" A "], " B ", [%9], %10, " P ";\n"
+#define SPST_COMMIT " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%12];\n"
+__device__ __forceinline__ void issue_chunk(int nterms, uint32_t d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                            uint64_t b0, uint64_t b1, uint64_t b2, uint64_t b3, uint32_t meta,
+                                            uint32_t idesc, uint32_t en, uint32_t bar) {
+#define SPST_CHUNK_OPERANDS                                                                                   \
+  "r"(d), "r"(a0), "r"(a1), "r"(a2), "r"(a3), "l"(b0), "l"(b1), "l"(b2), "l"(b3), "r"(meta), "r"(idesc), "r"(en), \
+      "r"(bar)
+  switch (nterms) {
+    case 1:
+      asm volatile("{\n .reg .pred e, q, t;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %11, 0;\n"
+                   " setp.eq.b32 t, %11, %11;\n" SPST_MMA_SP("%1", "%5", "q") SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS
+                   : "memory");
+      break;
+    case 2:
+      asm volatile("{\n .reg .pred e, q, t;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %11, 0;\n"
+                   " setp.eq.b32 t, %11, %11;\n" SPST_MMA_SP("%1", "%5", "q") SPST_MMA_SP("%2", "%6", "t")
+                       SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS
+                   : "memory");
+      break;
+    case 3:
+      asm volatile("{\n .reg .pred e, q, t;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %11, 0;\n"
+                   " setp.eq.b32 t, %11, %11;\n" SPST_MMA_SP("%1", "%5", "q") SPST_MMA_SP("%2", "%6", "t")
+                       SPST_MMA_SP("%3", "%7", "t") SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS
+                   : "memory");
+      break;
+    default:
+      asm volatile("{\n .reg .pred e, q, t;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %11, 0;\n"
+                   " setp.eq.b32 t, %11, %11;\n" SPST_MMA_SP("%1", "%5", "q") SPST_MMA_SP("%2", "%6", "t")
+                       SPST_MMA_SP("%3", "%7", "t") SPST_MMA_SP("%4", "%8", "t") SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS
+                   : "memory");
+      break;
+  }
+#undef SPST_CHUNK_OPERANDS
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi, int fp16) {
@@ -188,14 +256,16 @@ __device__ __forceinline__ void trace(bool on, int role, int li, int ev) {
   if (on && li < kTraceTiles) g_trace[(role * kTraceTiles + li) * 2 + ev] = gtimer();
 #endif
 }
-// Chunk-level clock64 stamps of gather warp 0 in CTA 0 for tile 1: [chunk < 16][4]
-// (chunk start, halo loads issued+LUT, slot free, chunk published).
-__device__ unsigned long long g_trace_chunks[16 * 4];
-__device__ __forceinline__ void trace_chunk(bool on, int kc, int ev) {
+// Chunk-level clock64 stamps in CTA 0 for tile 1: [source][chunk < 16][4], sources 0 and 1
+// the first and the last gather warp (chunk start, halo loads issued + LUT, slot free, chunk
+// published), source 2 the MMA issuer (chunk's B'' complete, MMAs issued, -, -).
+constexpr int kTraceChunkWords = 3 * 16 * 4 + 16 * 16;  // + [gather warp][chunk] publish stamps
+__device__ unsigned long long g_trace_chunks[kTraceChunkWords];
+__device__ __forceinline__ void trace_chunk(bool on, int src, int kc, int ev) {
   if (SPST_TRACE && on && kc < 16) {
     unsigned long long c;
     asm volatile("mov.u64 %0, %%clock64;" : "=l"(c));
-    g_trace_chunks[kc * 4 + ev] = c;
+    g_trace_chunks[(src * 16 + kc) * 4 + ev] = c;
   }
 }
 
@@ -209,19 +279,19 @@ struct SmemLayout {
     off_lut = off_b + slot_bytes * (uint32_t)p.nslots;
     off_cv = off_lut + (((uint32_t)p.kpad * 4u + 15u) & ~15u);
     off_bar = off_cv + 2u * 128u * 4u;
-    total = off_bar + 256u;
+    total = off_bar + 512u;
   }
 };
 
 // barrier indices (8 bytes each, from off_bar)
 constexpr int BAR_HFULL = 0, BAR_HEMPTY = 2, BAR_BFULL = 4, BAR_BEMPTY = 4 + kMaxBSlots,
               BAR_AFULL = 4 + 2 * kMaxBSlots, BAR_AEMPTY = BAR_AFULL + 2, BAR_CVFULL = BAR_AEMPTY + 2,
-              BAR_FINAL = BAR_CVFULL + 2;
-constexpr int BAR_COUNT = BAR_FINAL + 1;  // 27 barriers = 216 bytes, below the TMEM slot at +224
-static_assert(BAR_COUNT * 8 <= 224, "barrier area overlaps the TMEM slot");
+              BAR_CVEMPTY = BAR_CVFULL + 2, BAR_FINAL = BAR_CVEMPTY + 2;
+constexpr int BAR_COUNT = BAR_FINAL + 1;  // 29 barriers = 232 bytes, below the TMEM slot at +256
+static_assert(BAR_COUNT * 8 <= 256, "barrier area overlaps the TMEM slot");
 constexpr uint32_t TMEM_COLS = 512;
 
-constexpr int kGatherWarp0 = 8;                                 // warps 8 .. 23 build B''
+constexpr int kGatherWarp0 = 4 + kEpiWarps;                     // the last 16 warps build B''
 constexpr int kGatherWarps = kSweepThreads / 32 - kGatherWarp0;  // 16
 constexpr int kItems = 64 / kGatherWarps;                        // patch pairs per gather warp per chunk
 
@@ -236,8 +306,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t bar0 = sbase + L.off_bar;
   auto bar = [&](int i) -> uint32_t { return bar0 + 8u * (uint32_t)i; };
-  uint32_t* tmem_slot = (uint32_t*)(smem + L.off_bar + 224);               // 16-byte aligned
-  volatile int* abort_flag = (volatile int*)(smem + L.off_bar + 240);
+  uint32_t* tmem_slot = (uint32_t*)(smem + L.off_bar + 256);               // 16-byte aligned
+  volatile int* abort_flag = (volatile int*)(smem + L.off_bar + 272);
   int32_t* lut_s = (int32_t*)(smem + L.off_lut);
   const int pieces = p.a_pieces;
   const int acols = p.kpad / 4;
@@ -256,25 +326,15 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     }
     for (int a = 0; a < 2; a++) {
       mbar_init(bar(BAR_AFULL + a), 1);
-      mbar_init(bar(BAR_AEMPTY + a), 4);
+      mbar_init(bar(BAR_AEMPTY + a), kEpiWarps);
       mbar_init(bar(BAR_CVFULL + a), kGatherWarps);
+      mbar_init(bar(BAR_CVEMPTY + a), kEpiWarps);
     }
     mbar_init(bar(BAR_FINAL), 1);
     abort_flag[0] = 0;
     abort_flag[1] = 0;
     abort_flag[2] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
-    // the first tile's halo load overlaps the set-up below (when stage 0 is not needed for
-    // staging the A'' pieces)
-    if (p.early_tma && (int)blockIdx.x < p.num_tiles) {
-      const int tt = (int)blockIdx.x;
-      mbar_expect_tx(bar(BAR_HFULL), (uint32_t)p.box_h * (uint32_t)p.P * 4u);
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-              sbase),
-          "l"(&tmap_in), "r"((tt % p.tiles_x) * 128), "r"((tt / p.tiles_x) * 128), "r"(bar(BAR_HFULL))
-          : "memory");
-    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -288,7 +348,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   // TMEM (lane = output row of the patch).
   const int apitch = acols + 4;                       // words per staged A'' row
   const int mpitch = p.kchunks | 1;                   // words per staged metadata row (odd)
-  const uint32_t stage_a = sbase + (p.early_tma ? L.halo_stride : 0u);  // staging area (shared address)
+  const uint32_t stage_a = sbase;  // staging area (shared address)
   const uint32_t stage_m = stage_a + 4u * (uint32_t)(pieces * 128 * apitch);
   {
     const int q4 = acols / 4;  // uint4 per A'' row
@@ -343,6 +403,13 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
+  // Programmatic dependent launch: the set-up above reads only this launch's tables (written
+  // before the previous kernel started) and may overlap the previous sweep; the grids are
+  // read and written only after that sweep has completed and its writes are visible.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the next sweep may be scheduled now; its own griddepcontrol.wait orders its grid
+  // accesses after this grid's completion
+  asm volatile("griddepcontrol.launch_dependents;");
 
   const int ntiles_cta = (p.num_tiles > (int)blockIdx.x) ? (p.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const bool tr = (blockIdx.x == 0) && g_trace_on;
@@ -351,9 +418,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       const uint32_t bytes = (uint32_t)p.box_h * (uint32_t)p.P * 4u;
-      const int first = (p.early_tma && ntiles_cta > 0) ? 1 : 0;  // tile 0 was issued during set-up
-      int issued = first;
-      for (int li = first; li < ntiles_cta; li++) {
+      int issued = 0;
+      for (int li = 0; li < ntiles_cta; li++) {
         const int stage = li & 1;
         if (li >= 2 && !mbar_wait(bar(BAR_HEMPTY + stage), ((li >> 1) - 1) & 1, wait_ns, abort_flag, p.status)) break;
         const int tt = (int)blockIdx.x + li * (int)gridDim.x;
@@ -374,60 +440,76 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      uint32_t idesc = 0;
-      idesc |= 1u << 2;                      // sparse
-      idesc |= 1u << 4;                      // D = FP32
-      idesc |= (p.fp16 ? 0u : 1u) << 7;      // A: FP16 (0) / BF16 (1)
-      idesc |= (p.fp16 ? 0u : 1u) << 10;     // B: FP16 (0) / BF16 (1)
-      idesc |= (uint32_t)(128 >> 3) << 17;   // N = 128
-      idesc |= (uint32_t)(128 >> 4) << 24;   // M = 128
-      uint32_t mslot = 0, mphase = 0;  // chunk ring position and wrap parity
-      bool ok = true;
-      for (int li = 0; li < ntiles_cta && ok; li++) {
-        const int acc = li % nacc, use = li / nacc;
-        if (use > 0 && !mbar_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        trace(tr, 1, li, 0);
-        const uint32_t dcol = tmem + (uint32_t)(acc * 128);
-        for (int kc = 0; kc < p.kchunks; kc++) {
-          const uint32_t slot = mslot, su = mphase;
-          if (++mslot == (uint32_t)p.nslots) {
-            mslot = 0;
-            mphase ^= 1u;
-          }
-          if (!mbar_wait(bar(BAR_BFULL + slot), su & 1, wait_ns, abort_flag, p.status)) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t bslot = sbase + L.off_b + slot * L.slot_bytes;
-          const uint32_t meta = tmem + meta_col + 8u * (uint32_t)(kc >> 1);
-          const uint32_t idesc_kc = idesc | (uint32_t)(kc & 1);  // sparsity selector
-          for (int term = 0; term < p.nterms; term++) {
-            const uint32_t a_addr = tmem + a_col + (uint32_t)(p.term_a[term] * acols + kc * 8);
-            const uint64_t bdesc = make_sdesc(bslot + (uint32_t)(p.term_b[term] * kPieceBytes), kLBO, kSBO);
-            const uint32_t en = (kc > 0 || term > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n"
-                " tcgen05.mma.sp.cta_group::1.kind::f16 [%0], [%1], %2, [%3], %4, q;\n}" ::"r"(dcol),
-                "r"(a_addr), "l"(bdesc), "r"(meta), "r"(idesc_kc), "r"(en));
-          }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              bar(BAR_BEMPTY + slot)));
-        }
-        if (!ok) break;
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            bar(BAR_AFULL + acc)));
-        trace(tr, 1, li, 1);
-      }
-      // every MMA issued above completes before TMEM is released
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(BAR_FINAL)));
-      mbar_wait(bar(BAR_FINAL), 0, kDrainNs, nullptr, p.status);
+    // The whole warp runs the loop (warp-uniform waits and addresses) and one elected lane
+    // issues each tcgen05 instruction.  The per-term operand addresses are fixed before the
+    // tile loop, so an MMA costs an add or two: the issue loop is a single latency chain, and
+    // at about 70 cycles per sparse 128x128x32 MMA any dependent work in it is exposed.
+    uint32_t idesc = 0;
+    idesc |= 1u << 2;                      // sparse
+    idesc |= 1u << 4;                      // D = FP32
+    idesc |= (p.fp16 ? 0u : 1u) << 7;      // A: FP16 (0) / BF16 (1)
+    idesc |= (p.fp16 ? 0u : 1u) << 10;     // B: FP16 (0) / BF16 (1)
+    idesc |= (uint32_t)(128 >> 3) << 17;   // N = 128
+    idesc |= (uint32_t)(128 >> 4) << 24;   // M = 128
+    const int nterms = p.nterms;
+    uint32_t a_term[4], b_term[4];  // TMEM address of the term's A'' piece; B piece offset (16-byte units)
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      a_term[t] = tmem + a_col + (uint32_t)((t < nterms ? p.term_a[t] : 0) * acols);
+      b_term[t] = (uint32_t)((t < nterms ? p.term_b[t] : 0) * (kPieceBytes >> 4));
     }
-  } else if (warp >= 4 && warp < 8) {
+    // descriptor of slot 0, piece 0; the start-address field (bits 0-13, 16-byte units) of
+    // any slot and piece stays below 2^14 (shared memory < 256 KB), so offsets add to the low word
+    const uint64_t desc0 = make_sdesc(sbase + L.off_b, kLBO, kSBO);
+    const uint32_t dlo0 = (uint32_t)desc0, dhi = (uint32_t)(desc0 >> 32);
+    const uint32_t slot_step = L.slot_bytes >> 4;
+    uint32_t mslot = 0, mphase = 0;  // chunk ring position and wrap parity
+    bool ok = true;
+    for (int li = 0; li < ntiles_cta && ok; li++) {
+      const int acc = li % nacc, use = li / nacc;
+      if (use > 0 && !warp_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      trace(tr && lane == 0, 1, li, 0);
+      const uint32_t dcol = tmem + (uint32_t)(acc * 128);
+      for (int kc = 0; kc < p.kchunks; kc++) {
+        const uint32_t slot = mslot, su = mphase;
+        if (++mslot == (uint32_t)p.nslots) {
+          mslot = 0;
+          mphase ^= 1u;
+        }
+        if (!warp_wait(bar(BAR_BFULL + slot), su & 1, wait_ns, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        trace_chunk(tr && li == 1 && lane == 0, 2, kc, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t blo = dlo0 + slot * slot_step;
+        const uint32_t meta = tmem + meta_col + 8u * (uint32_t)(kc >> 1);
+        const uint32_t idesc_kc = idesc | (uint32_t)(kc & 1);  // sparsity selector
+        const uint32_t a8 = 8u * (uint32_t)kc;
+        const uint64_t b0 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[0]);
+        const uint64_t b1 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[1]);
+        const uint64_t b2 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[2]);
+        const uint64_t b3 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[3]);
+        issue_chunk(nterms, dcol, a_term[0] + a8, a_term[1] + a8, a_term[2] + a8, a_term[3] + a8, b0, b1, b2, b3, meta,
+                    idesc_kc, kc > 0 ? 1u : 0u, bar(BAR_BEMPTY + slot));
+        trace_chunk(tr && li == 1 && lane == 0, 2, kc, 1);
+      }
+      if (!ok) break;
+      commit_elected(bar(BAR_AFULL + acc));
+      trace(tr && lane == 0, 1, li, 1);
+    }
+    // every MMA issued above completes before TMEM is released
+    commit_elected(bar(BAR_FINAL));
+    if (lane == 0) mbar_wait(bar(BAR_FINAL), 0, kDrainNs, nullptr, p.status);
+    __syncwarp();
+  } else if (warp >= 4 && warp < 4 + kEpiWarps) {
     // ---------------- epilogue ----------------
-    const int q = warp - 4;
+    // warp 4 + q + 4h reads TMEM lanes 32q .. 32q+31 (its lane quarter) and, with 8 epilogue
+    // warps, accumulator columns 64h .. 64h+63
+    const int q = (warp - 4) & 3;
+    constexpr int kGroups = 8 / (kEpiWarps / 4);  // 16-column groups per warp
+    const int cg0 = ((warp - 4) >> 2) * kGroups;
     const int rho = 32 * q + lane;
     const int ry = rho >> 4, rx = rho & 15;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
@@ -437,7 +519,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     for (int li = 0; li < ntiles_cta; li++) {
       const int acc = li % nacc, use = li / nacc;
       if (!warp_wait(bar(BAR_AFULL + acc), use & 1, wait_ns, abort_flag, p.status)) break;
-      if (!warp_wait(bar(BAR_CVFULL + acc), use & 1, wait_ns, abort_flag, p.status)) break;
+      if (!warp_wait(bar(BAR_CVFULL + (li & 1)), (li >> 1) & 1, wait_ns, abort_flag, p.status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       trace(tr && warp == 4 && lane == 0, 3, li, 0);
       const int tt = (int)blockIdx.x + li * (int)gridDim.x;
@@ -448,7 +530,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       const bool ghost = p.out_ghost && (y0 < G || y0 + 128 > p.H - G || x0 < G || x0 + 128 > p.W - G);
       float* obase = p.out + (int64_t)(y0 + G + ry) * p.out_pitch + (x0 + G + rx);
 #pragma unroll 1
-      for (int cg = 0; cg < 8; cg++) {
+      for (int cg = cg0; cg < cg0 + kGroups; cg++) {
         uint32_t v[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -456,7 +538,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(lane_addr + (uint32_t)(acc * 128 + cg * 16)));
         float c[16];
-        const uint32_t ca = cv_s + (uint32_t)(acc * 128 + cg * 16) * 4u;
+        const uint32_t ca = cv_s + (uint32_t)((li & 1) * 128 + cg * 16) * 4u;
 #pragma unroll
         for (int k4 = 0; k4 < 4; k4++) {
           const float4 c4 = lds_v4_f32(ca + 16u * k4);
@@ -497,7 +579,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar(BAR_AEMPTY + acc));
+      if (lane == 0) {
+        mbar_arrive(bar(BAR_AEMPTY + acc));
+        mbar_arrive(bar(BAR_CVEMPTY + (li & 1)));
+      }
       trace(tr && warp == 4 && lane == 0, 3, li, 1);
     }
   } else if (warp >= kGatherWarp0) {
@@ -525,7 +610,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     }
     const uint32_t lut_sa = sbase + L.off_lut + 8u * (uint32_t)pl;
     for (int li = 0; li < ntiles_cta; li++) {
-      const int stage = li & 1, acc = li % nacc, use = li / nacc;
+      const int stage = li & 1;
       if (!warp_wait(bar(BAR_HFULL + stage), (li >> 1) & 1, wait_ns, abort_flag, p.status)) break;
       trace(tr && gw == 0 && lane == 0, 2, li, 0);
       const uint32_t tile_s = sbase + (uint32_t)stage * L.halo_stride;
@@ -534,34 +619,53 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 #pragma unroll
       for (int i = 0; i < kItems; i++) {
         ba[i] = tile_s + (uint32_t)base_i[i];
-        c_i[i] = lds_f32(ba[i] + 4u * (uint32_t)(G * P + G));
+        // the patch constant: the input value at the patch centre (row 4, column 8 of its
+        // 8 x 16 outputs), which keeps |u - c| small over the patch's whole stencil window
+        c_i[i] = lds_f32(ba[i] + 4u * (uint32_t)((G + 4) * P + G + 8));
       }
-      if (use > 0 && !warp_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
+      // the patch constants go to a two-slot area of their own, so that building B'' for this
+      // tile never waits for the epilogue that is draining the accumulator
+      const int cvs = li & 1;
+      if (li >= 2 && !warp_wait(bar(BAR_CVEMPTY + cvs), ((li >> 1) - 1) & 1, wait_ns, abort_flag, p.status)) break;
       if (pl == 0) {
 #pragma unroll
-        for (int i = 0; i < kItems; i++) sts_f32(sbase + L.off_cv + 4u * (uint32_t)(acc * 128 + n_i[i]), c_i[i]);
+        for (int i = 0; i < kItems; i++) sts_f32(sbase + L.off_cv + 4u * (uint32_t)(cvs * 128 + n_i[i]), c_i[i]);
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar(BAR_CVFULL + acc));
+      if (lane == 0) mbar_arrive(bar(BAR_CVFULL + cvs));
       bool ok = true;
-      const bool trc = tr && gw == 0 && lane == 0 && li == 1;
-      for (int kc = 0; kc < p.kchunks; kc++) {
-        trace_chunk(trc, kc, 0);
-        const int2 lab = lds_v2_s32(lut_sa + 128u * (uint32_t)kc);
+      const bool trc = tr && (gw == 0 || gw == kGatherWarps - 1) && lane == 0 && li == 1;
+      const int tsrc = gw == 0 ? 0 : 1;
+      // software pipeline: chunk kc+1's loads are issued before chunk kc's values are used
+      float va[kItems], vb[kItems];
+      {
+        const int2 lab = lds_v2_s32(lut_sa);
         const uint32_t la = 4u * (uint32_t)lab.x, lb = 4u * (uint32_t)lab.y;
-        float va[kItems], vb[kItems];
 #pragma unroll
         for (int i = 0; i < kItems; i++) {
           va[i] = lds_f32(ba[i] + la);
           vb[i] = lds_f32(ba[i] + lb);
         }
-        trace_chunk(trc, kc, 1);
+      }
+      for (int kc = 0; kc < p.kchunks; kc++) {
+        trace_chunk(trc, tsrc, kc, 0);
+        float na[kItems], nb[kItems];
+        if (kc + 1 < p.kchunks) {
+          const int2 lab = lds_v2_s32(lut_sa + 128u * (uint32_t)(kc + 1));
+          const uint32_t la = 4u * (uint32_t)lab.x, lb = 4u * (uint32_t)lab.y;
+#pragma unroll
+          for (int i = 0; i < kItems; i++) {
+            na[i] = lds_f32(ba[i] + la);
+            nb[i] = lds_f32(ba[i] + lb);
+          }
+        }
+        trace_chunk(trc, tsrc, kc, 1);
         if (used >= (uint32_t)p.nslots &&
             !warp_wait(bar(BAR_BEMPTY + slot), sphase ^ 1u, wait_ns, abort_flag, p.status)) {
           ok = false;
           break;
         }
-        trace_chunk(trc, kc, 2);
+        trace_chunk(trc, tsrc, kc, 2);
         const uint32_t bs = sbase + L.off_b + slot * L.slot_bytes;
 #pragma unroll
         for (int i = 0; i < kItems; i++) {
@@ -578,12 +682,24 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(BAR_BFULL + slot));
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+          va[i] = na[i];
+          vb[i] = nb[i];
+        }
         used++;
         if (++slot == (uint32_t)p.nslots) {
           slot = 0;
           sphase ^= 1u;
         }
-        trace_chunk(trc, kc, 3);
+        trace_chunk(trc, tsrc, kc, 3);
+#if SPST_TRACE
+        if (tr && li == 1 && lane == 0 && kc < 16) {
+          unsigned long long c;
+          asm volatile("mov.u64 %0, %%clock64;" : "=l"(c));
+          g_trace_chunks[3 * 16 * 4 + gw * 16 + kc] = c;
+        }
+#endif
       }
       if (!ok) break;
       __syncwarp();
@@ -608,7 +724,8 @@ cudaError_t sweep_trace_enable(int on) {
   cudaError_t e = cudaMemcpyToSymbol(g_trace_on, &on, sizeof(int));
   if (e != cudaSuccess) return e;
   static const unsigned long long zeros[4 * kTraceTiles * 2] = {0};
-  e = cudaMemcpyToSymbol(g_trace_chunks, zeros, 64 * sizeof(unsigned long long));
+  static const unsigned long long zc[kTraceChunkWords] = {0};
+  e = cudaMemcpyToSymbol(g_trace_chunks, zc, sizeof(zc));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(g_trace, zeros, sizeof(zeros));
 }
@@ -617,7 +734,7 @@ cudaError_t sweep_trace_read(unsigned long long* out, int n) {
   const int n1 = 4 * kTraceTiles * 2;
   cudaError_t e = cudaMemcpyFromSymbol(out, g_trace, (size_t)(n < n1 ? n : n1) * sizeof(unsigned long long));
   if (e != cudaSuccess || n <= n1) return e;
-  const int n2 = (n - n1 < 64) ? n - n1 : 64;
+  const int n2 = (n - n1 < kTraceChunkWords) ? n - n1 : kTraceChunkWords;
   return cudaMemcpyFromSymbol(out + n1, g_trace_chunks, (size_t)n2 * sizeof(unsigned long long));
 }
 
@@ -663,8 +780,17 @@ cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p_in
   if (e != cudaSuccess) return e;
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, kSweepThreads, smem, stream>>>(tmap_in, p);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kSweepThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, tmap_in, p);
 }
 
 }  // namespace spst

@@ -8,7 +8,7 @@ z_i = mix64(seed + (i + 1) * 0x9E3779B97F4A7C15).
   * uniform [0, 1) FP32  = (z >> 40) * 2^-24   (exact in FP32)
   * uniform [-1, 1) FP32 = 2 * u - 1           (exact in FP32)
 
-Weight recipes (the paper's workloads, Table 2, with the BASELINE configs' weights):
+Weight recipes (the paper's workloads, Table 2, with the benchmark workloads' weights):
   * 'heat'      — Heat-2D/3D: centre 0.5, each axis neighbour 0.5 / (2 * ndim) ... for 2D
                   this is centre 0.5 and four neighbours 0.125 (exact in FP16/BF16).
   * 'random'    — seeded positive U[0.05, 1) per stencil point, normalised to sum 1 in

@@ -47,6 +47,12 @@ CASES = [
     ("box", 3, "gaussian", (260, 300), 6, "periodic", "bf16", 1),
     ("box", 3, "gaussian", (200, 256), 5, "dirichlet", "fp16_split", 1),
     ("box", 2, "random", (128, 128), 4, "periodic", "bf16_split", 1),
+    # Dirichlet with temporal fusion: the fused kernel plus the exact band of width (t-1)r
+    ("star", 1, "heat", (512, 512), 8, "dirichlet", "fp16", 3),
+    ("star", 1, "heat", (512, 512), 8, "dirichlet", "bf16_split", 3),
+    ("box", 1, "random", (130, 200), 10, "dirichlet", "bf16_split", 4),
+    ("box", 2, "gaussian", (300, 260), 7, "dirichlet", "bf16_split", 2),
+    ("star", 3, "gaussian", (260, 300), 9, "dirichlet", "bf16", 2),
 ]
 
 
@@ -59,6 +65,13 @@ def test_sparse_matches_oracle(torch_cuda, oracle_mod, shape, r, recipe, dims, s
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
     assert l2 <= TOL[dtype], (l2, linf)
+    if bc == "dirichlet" and t > 1:
+        # the frame the fused kernel cannot produce must meet the tolerance on its own
+        bw = (t - 1) * r
+        band = np.ones(dims, dtype=bool)
+        band[bw:-bw, bw:-bw] = False
+        bl2 = np.sqrt(np.sum((got[band] - ref[band]) ** 2) / np.sum(ref[band] ** 2))
+        assert bl2 <= TOL[dtype], bl2
 
 
 def test_zero_and_one_step(torch_cuda, oracle_mod):
@@ -88,6 +101,23 @@ def test_closed_form_fourier_mode(torch_cuda):
     got, _ = _run_sparse(torch_cuda, u0, w, T, "bf16_split", "periodic", 1, "box")
     err = np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2))
     assert err <= 1e-5, err
+
+
+def test_closed_form_sine_mode_dirichlet_fused(torch_cuda):
+    """Dirichlet closed form, no oracle: for the Heat-2D star the zero-boundary sine mode
+    u0 = sin(pi p (y+1)/(H+1)) sin(pi q (x+1)/(W+1)) is an eigenvector with eigenvalue
+    lambda = 1/2 + 1/4 cos(pi p/(H+1)) + 1/4 cos(pi q/(W+1)); 100 steps fused 3 at a time
+    (the band path supplies the frame the fused kernel cannot)."""
+    H, W, pm, qm, T = 250, 300, 2, 3, 100
+    w = inputs.stencil_weights("star", 2, 1, "heat", seed=0)
+    y, x = np.mgrid[0:H, 0:W]
+    u0 = np.sin(np.pi * pm * (y + 1) / (H + 1)) * np.sin(np.pi * qm * (x + 1) / (W + 1))
+    lam = 0.5 + 0.25 * np.cos(np.pi * pm / (H + 1)) + 0.25 * np.cos(np.pi * qm / (W + 1))
+    u32 = u0.astype(np.float32)
+    ref = lam ** T * u32.astype(np.float64)
+    got, _ = _run_sparse(torch_cuda, u32, w, T, "bf16_split", "dirichlet", 3, "star")
+    l2 = np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2))
+    assert l2 <= 1e-5, l2
 
 
 def test_direct_fp32_matches_oracle(torch_cuda, oracle_mod):

@@ -115,10 +115,15 @@ def test_planner_tables_against_oracle(lib, oracle_mod, shape, r, recipe, t, dty
     assert morph.satisfies_2_4(dense_hi) and morph.satisfies_2_4(dense_hi + dense_lo)
     Ap = morph.apply_permutation(A, list(order))
     np.testing.assert_array_equal(dense_hi, rnd(Ap * sc) / sc)
-    if split and not fp16:
+    # weight pieces: split operands use three (two for a fused sweep that needs the TMEM for a
+    # second accumulator), single-word operands two; one MMA term per piece, plus one for the
+    # data's low part with split operands
+    pieces = info.mma_terms - (1 if split else 0)
+    assert pieces in (1, 2, 3) and (pieces == 3 or not split or t >= 2)
+    if pieces == 3 and not fp16:
         # three BF16 pieces hold every FP32 weight exactly
         np.testing.assert_array_equal(dense_hi + dense_lo, Ap)
-    elif split:
+    elif pieces == 3:
         # FP16's third piece is limited by the subnormal step 2^-24 of the scaled weights
         assert np.max(np.abs(dense_hi + dense_lo - Ap)) <= 2.0 ** -24 * np.max(np.abs(wf32))
     else:
