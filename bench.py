@@ -57,12 +57,15 @@ def _peaks():
 
 def _profile_traffic():
     """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary, if the
-    summary was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2506_22969_gb300", "csrc", "sweep2d.cu")
+    summary was taken on the current kernel source (sweep2d.cu + kernels.h; else None)."""
+    csrc = os.path.join(ROOT, "paper_2506_22969_gb300", "csrc")
     prof = os.path.join(ROOT, "profiles", "sweep2d_box9_4096.md")
     try:
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for name in ("sweep2d.cu", "kernels.h"):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+        sha = h.hexdigest()[:16]
         with open(prof) as f:
             text = f.read()
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
@@ -89,7 +92,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -319,6 +322,11 @@ def main():
                 best = (t, ms, pl)
         return best
 
+    # clocks: sampled every 20 ms from the start of the fusion-depth search (about a second
+    # of the same sweeps) to the end of the timed runs, so that short timed regions still
+    # get samples
+    clocks = ClockSampler(local)
+    clocks.start()
     t_best, _, plan = autotune("bf16_split")
     info = plan.info()
 
@@ -334,12 +342,11 @@ def main():
 
     if dist is not None:
         dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
     torch.cuda.synchronize()
     run_ms = timed_runs(lambda: plan.run(x, y, T), args.steps, args.warmup)
     torch.cuda.synchronize()
     clock_info = clocks.stop()
+    clock_info["window"] = "fusion-depth search + warm-up + timed runs, 20 ms period"
     if dist is not None:
         dist.barrier()
     tot = sum(run_ms)
