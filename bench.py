@@ -244,7 +244,8 @@ def trace_case():
                                    f"free {ch[s, kc, 2] - c0:6d} pub {ch[s, kc, 3] - c0:6d}" for s in (0, 1))
                     print(f"  tile 1 chunk {kc:2d}: {g} | mma ready {ch[2, kc, 0] - c0:6d} "
                           f"issued {ch[2, kc, 1] - c0:6d} (cycles)")
-                    print("      publish by gather warp: " + " ".join(f"{pub[w, kc] - c0:6d}" for w in range(16)))
+                    print("      stored  by gather warp: " + " ".join(f"{pub[1, w, kc] - c0:6d}" for w in range(16)))
+                    print("      publish by gather warp: " + " ".join(f"{pub[0, w, kc] - c0:6d}" for w in range(16)))
 
 
 def main():

@@ -207,7 +207,8 @@ sparstencil_status sparstencil_trace(int enable);
  * the K chunks of CTA 0's second tile, [source][chunk < 16][4]: sources 0 and 1 the first and
  * the last B'' gather warp (chunk start, halo values loaded, chunk slot free, chunk
  * published), source 2 the MMA issuer (chunk complete in shared memory, MMAs issued);
- * entries 704..959: [gather warp < 16][chunk < 16] publish stamps of the same tile. */
+ * entries 704..959: [gather warp < 16][chunk < 16] publish stamps of the same tile;
+ * entries 960..1215: the same warps' stamps just before the chunk's proxy fence. */
 sparstencil_status sparstencil_trace_read(uint64_t* out, int n);
 
 /* Thread-local description of the last failure in this thread ("" if none). */

@@ -247,12 +247,12 @@ def trace(enable: bool):
 def trace_read():
     """(tiles, chunks, publish): tiles = int64 [role(TMA, MMA, gather, epilogue)][tile<64][start,
     end] in ns; chunks = int64 [source(first gather warp, last gather warp, MMA issuer)][chunk<16][4]
-    and publish = int64 [gather warp][chunk<16] in clock cycles."""
-    out = np.zeros(4 * 64 * 2 + 3 * 16 * 4 + 16 * 16, np.uint64)
+    and publish = int64 [publish, stores done][gather warp][chunk<16] in clock cycles."""
+    out = np.zeros(4 * 64 * 2 + 3 * 16 * 4 + 2 * 16 * 16, np.uint64)
     _check(load().sparstencil_trace_read(out.ctypes.data, out.size))
     tiles = out[:512].reshape(4, 64, 2).astype(np.int64)
     chunks = out[512:512 + 192].reshape(3, 16, 4).astype(np.int64)
-    return tiles, chunks, out[512 + 192:].reshape(16, 16).astype(np.int64)
+    return tiles, chunks, out[512 + 192:].reshape(2, 16, 16).astype(np.int64)
 
 
 def run_batch(plans, xs, outs, steps, stream=None):

@@ -307,6 +307,146 @@ int arrange_pairs(const std::vector<std::pair<int, int>>& pairs, const std::vect
   return repeats;
 }
 
+// Packs pairs into chunks of `slots` pairs with as few residue repeats as a local search
+// finds, for when no conflict-free packing in the minimum number of chunks exists.  A repeat
+// is a second column offset of the same residue mod 16 on the same side (first or second
+// columns) of one chunk: it costs the gather one extra shared-memory wavefront.  Offsets of
+// -1 mark zero columns, which read any word (their weights are zero) and so take a residue
+// the chunk's side does not use.  Moves: exchange two pairs (or a pair and an empty slot)
+// between chunks, each pair in either orientation, accepted when the repeat count does not
+// grow; a fixed-seed generator keeps the result deterministic.  Returns the repeat count.
+int pack_pairs_min_repeats(const std::vector<std::pair<int, int>>& pairs, const std::vector<std::pair<int, int>>& offs,
+                           int slots, std::vector<int>* order_out, std::vector<int32_t>* lut_out) {
+  const int n = (int)pairs.size();
+  const int nch = std::max(1, (n + slots - 1) / slots);
+  const int nslot = nch * slots;
+  auto res = [](int o) { return o < 0 ? -1 : ((o % 16) + 16) % 16; };
+  // slot s holds item it[s] (-1 empty) with flip fl[s]
+  std::vector<int> it(nslot, -1);
+  std::vector<char> fl(nslot, 0);
+  for (int i = 0; i < n; i++) it[i] = i;
+  auto rA = [&](int s) { return it[s] < 0 ? -1 : res(fl[s] ? offs[it[s]].second : offs[it[s]].first); };
+  auto rB = [&](int s) { return it[s] < 0 ? -1 : res(fl[s] ? offs[it[s]].first : offs[it[s]].second); };
+  std::vector<int> cA(nch * 16, 0), cB(nch * 16, 0);
+  for (int s = 0; s < nslot; s++) {
+    const int c = s / slots, a = rA(s), b = rB(s);
+    if (a >= 0) cA[c * 16 + a]++;
+    if (b >= 0) cB[c * 16 + b]++;
+  }
+  int total = 0;
+  for (int i = 0; i < nch * 16; i++) total += std::max(0, cA[i] - 1) + std::max(0, cB[i] - 1);
+  // repeat-count change when residue r leaves (d = -1) or joins (d = +1) counter x
+  auto dlt = [](int x, int d) { return d > 0 ? (x >= 1 ? 1 : 0) : (x >= 2 ? -1 : 0); };
+  uint64_t st = 0x9E3779B97F4A7C15ull;
+  auto rnd = [&](uint64_t m) {
+    st ^= st << 13;
+    st ^= st >> 7;
+    st ^= st << 17;
+    return (int)(st % m);
+  };
+  // a lower bound: a residue carried by more columns than the chunk sides offer repeats
+  int bound = 0;
+  {
+    int deg[16] = {0};
+    for (int i = 0; i < n; i++) {
+      if (res(offs[i].first) >= 0) deg[res(offs[i].first)]++;
+      if (res(offs[i].second) >= 0) deg[res(offs[i].second)]++;
+    }
+    for (int v = 0; v < 16; v++) bound += std::max(0, deg[v] - 2 * nch);
+  }
+  std::vector<int> best_it = it;
+  std::vector<char> best_fl = fl;
+  int best = total;
+  const long iters = 300000;
+  for (long k = 0; k < iters && best > bound; k++) {
+    const int s1 = rnd(nslot), s2 = rnd(nslot);
+    const int c1 = s1 / slots, c2 = s2 / slots;
+    if (c1 == c2 || (it[s1] < 0 && it[s2] < 0)) continue;
+    const int f1 = rnd(2), f2 = rnd(2);  // new orientations of the items moving into c2 / c1
+    auto resA = [&](int s, int f) { return it[s] < 0 ? -1 : res(f ? offs[it[s]].second : offs[it[s]].first); };
+    auto resB = [&](int s, int f) { return it[s] < 0 ? -1 : res(f ? offs[it[s]].first : offs[it[s]].second); };
+    const int a1 = rA(s1), b1 = rB(s1), a2 = rA(s2), b2 = rB(s2);
+    const int na1 = resA(s1, f1), nb1 = resB(s1, f1), na2 = resA(s2, f2), nb2 = resB(s2, f2);
+    // item of s1 leaves c1 and joins c2; item of s2 leaves c2 and joins c1
+    int d = 0;
+    if (a1 >= 0) { d += dlt(cA[c1 * 16 + a1], -1); cA[c1 * 16 + a1]--; }
+    if (b1 >= 0) { d += dlt(cB[c1 * 16 + b1], -1); cB[c1 * 16 + b1]--; }
+    if (a2 >= 0) { d += dlt(cA[c2 * 16 + a2], -1); cA[c2 * 16 + a2]--; }
+    if (b2 >= 0) { d += dlt(cB[c2 * 16 + b2], -1); cB[c2 * 16 + b2]--; }
+    if (na1 >= 0) { d += dlt(cA[c2 * 16 + na1], +1); cA[c2 * 16 + na1]++; }
+    if (nb1 >= 0) { d += dlt(cB[c2 * 16 + nb1], +1); cB[c2 * 16 + nb1]++; }
+    if (na2 >= 0) { d += dlt(cA[c1 * 16 + na2], +1); cA[c1 * 16 + na2]++; }
+    if (nb2 >= 0) { d += dlt(cB[c1 * 16 + nb2], +1); cB[c1 * 16 + nb2]++; }
+    // annealing: a move that adds one repeat is taken with a probability falling from 1/8
+    // to 0 over the run
+    const bool take = d <= 0 || (d == 1 && (uint64_t)rnd(1u << 20) < (uint64_t)((1u << 17) * (iters - k) / iters));
+    if (take) {
+      std::swap(it[s1], it[s2]);
+      fl[s2] = (char)f1;
+      fl[s1] = (char)f2;
+      total += d;
+      if (total < best) {
+        best = total;
+        best_it = it;
+        best_fl = fl;
+      }
+    } else {  // undo
+      if (na1 >= 0) cA[c2 * 16 + na1]--;
+      if (nb1 >= 0) cB[c2 * 16 + nb1]--;
+      if (na2 >= 0) cA[c1 * 16 + na2]--;
+      if (nb2 >= 0) cB[c1 * 16 + nb2]--;
+      if (a1 >= 0) cA[c1 * 16 + a1]++;
+      if (b1 >= 0) cB[c1 * 16 + b1]++;
+      if (a2 >= 0) cA[c2 * 16 + a2]++;
+      if (b2 >= 0) cB[c2 * 16 + b2]++;
+    }
+  }
+  it = best_it;
+  fl = best_fl;
+  total = best;
+  std::vector<int>& order = *order_out;
+  std::vector<int32_t>& lut = *lut_out;
+  order.clear();
+  lut.clear();
+  for (int c = 0; c < nch; c++) {
+    int ua[16] = {0}, ub[16] = {0};
+    for (int j = 0; j < slots; j++) {
+      const int s = c * slots + j;
+      if (rA(s) >= 0) ua[rA(s)]++;
+      if (rB(s) >= 0) ub[rB(s)]++;
+    }
+    for (int j = 0; j < slots; j++) {
+      const int s = c * slots + j;
+      int ca = -1, cb = -1, oa = -1, ob = -1;
+      if (it[s] >= 0) {
+        const int e = it[s];
+        ca = fl[s] ? pairs[e].second : pairs[e].first;
+        cb = fl[s] ? pairs[e].first : pairs[e].second;
+        oa = fl[s] ? offs[e].second : offs[e].first;
+        ob = fl[s] ? offs[e].first : offs[e].second;
+      }
+      // zero columns read row 0 of the patch window at a residue this side does not use
+      if (oa < 0) {
+        int r = 0;
+        while (r < 15 && ua[r]) r++;
+        ua[r]++;
+        oa = r;
+      }
+      if (ob < 0) {
+        int r = 0;
+        while (r < 15 && ub[r]) r++;
+        ub[r]++;
+        ob = r;
+      }
+      order.push_back(ca);
+      order.push_back(cb);
+      lut.push_back(oa);
+      lut.push_back(ob);
+    }
+  }
+  return total;
+}
+
 // ---------------------------------------------------------------------------------------
 // 2D sweep tables.
 // ---------------------------------------------------------------------------------------
@@ -369,6 +509,8 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   auto off = [&](int col) { return (col / g + geo.G - R) * geo.P + (col % g + geo.G - R); };
   std::vector<std::pair<int, int>> offs;
   for (auto& pr : kept) offs.push_back({off(pr.first), pr.second >= 0 ? off(pr.second) : off(pr.first)});
+  std::vector<std::pair<int, int>> offs_free;  // zero partners marked -1: they may read any word
+  for (auto& pr : kept) offs_free.push_back({off(pr.first), pr.second >= 0 ? off(pr.second) : -1});
   // Each matched pair holds at most one nonzero per row (its columns are >= kt apart, or one
   // is a zero column), so any two pairs form a valid group of four: the pairs may be
   // reordered and each pair's two columns swapped without breaking 2:4.  Use that freedom
@@ -380,26 +522,9 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   std::vector<int> order;
   std::vector<int32_t> lut;
   if (arrange_pairs(kept, offs, Tile2D::KCHUNK / 2, &order, &lut) < 0) {
-    // keep Algorithm 1's order; count the residue repeats the gather will meet
-    order.clear();
-    lut.clear();
-    for (size_t i = 0; i < kept.size(); i++) {
-      order.push_back(kept[i].first);
-      order.push_back(kept[i].second);
-      lut.push_back(offs[i].first);
-      lut.push_back(offs[i].second);
-    }
-    while (order.size() % Tile2D::KCHUNK) {
-      order.push_back(-1);
-      lut.push_back(0);
-    }
-    T.bank_conflicts = 0;
-    for (size_t k0 = 0; k0 < order.size(); k0 += Tile2D::KCHUNK)
-      for (int side = 0; side < 2; side++) {
-        int seen[16] = {0};
-        for (int j = side; j < Tile2D::KCHUNK; j += 2)
-          if (seen[((lut[k0 + j] % 16) + 16) % 16]++) T.bank_conflicts++;
-      }
+    // no conflict-free packing in the minimum number of chunks: the fewest repeats a local
+    // search finds, starting from Algorithm 1's order
+    T.bank_conflicts = pack_pairs_min_repeats(kept, offs_free, Tile2D::KCHUNK / 2, &order, &lut);
   }
   T.order = order;
   const int kpad = (int)order.size();

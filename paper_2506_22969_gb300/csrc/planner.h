@@ -80,6 +80,12 @@ std::vector<std::pair<int, int>> hierarchical_matching(int n, int g, int k);
 int arrange_pairs(const std::vector<std::pair<int, int>>& pairs, const std::vector<std::pair<int, int>>& offs,
                   int slots, std::vector<int>* order_out, std::vector<int32_t>* lut_out);
 
+// Packs pairs into chunks of `slots` pairs with as few bank repeats as a fixed-seed local
+// search finds (offsets of -1 mark zero columns, free to read any word); fills order/lut and
+// returns the number of repeats.
+int pack_pairs_min_repeats(const std::vector<std::pair<int, int>>& pairs, const std::vector<std::pair<int, int>>& offs,
+                           int slots, std::vector<int>* order_out, std::vector<int32_t>* lut_out);
+
 // Builds the sweep tables of a 2D stencil (fused cube `wfused` of radius R) for the Tile2D
 // kernel geometry, the ghost width G and tile pitch P of `geo`, and operand encoding `word`.
 // max_pieces: number of 16-bit pieces the weights may use (1..3).  Returns an empty string

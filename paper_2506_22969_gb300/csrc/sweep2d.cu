@@ -259,7 +259,7 @@ __device__ __forceinline__ void trace(bool on, int role, int li, int ev) {
 // Chunk-level clock64 stamps in CTA 0 for tile 1: [source][chunk < 16][4], sources 0 and 1
 // the first and the last gather warp (chunk start, halo loads issued + LUT, slot free, chunk
 // published), source 2 the MMA issuer (chunk's B'' complete, MMAs issued, -, -).
-constexpr int kTraceChunkWords = 3 * 16 * 4 + 16 * 16;  // + [gather warp][chunk] publish stamps
+constexpr int kTraceChunkWords = 3 * 16 * 4 + 2 * 16 * 16;  // + [gather warp][chunk] publish / stored stamps
 __device__ unsigned long long g_trace_chunks[kTraceChunkWords];
 __device__ __forceinline__ void trace_chunk(bool on, int src, int kc, int ev) {
   if (SPST_TRACE && on && kc < 16) {
@@ -679,6 +679,13 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
             sts_u32(bs + kPieceBytes + soff_i[i], pack2(da - ha, db - hb, FP16));
           }
         }
+#if SPST_TRACE
+        if (tr && li == 1 && lane == 0 && kc < 16) {
+          unsigned long long c;
+          asm volatile("mov.u64 %0, %%clock64;" : "=l"(c)::"memory");
+          g_trace_chunks[3 * 16 * 4 + 16 * 16 + gw * 16 + kc] = c;
+        }
+#endif
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(BAR_BFULL + slot));
