@@ -79,8 +79,11 @@ typedef struct {
 /* Builds a plan for `shape` stencils of radius `radius` on an ndim grid of extents dims.
  *   weights: host FP32 cube (see conventions), copied; for SPST_STAR/SPST_BOX only the
  *            shape's points may be nonzero (checked), SPST_CUSTOM accepts any support.
- *   fusion_depth: t >= 1 fuses t steps per sweep; 0 lets the library choose (autotuned
- *            on the first sparstencil_run, timed on the bound workspace).
+ *   fusion_depth: t >= 1 fuses t steps per sweep; 0 lets the library choose: the plan
+ *            takes the deepest of 3, 2, 1 whose tables fit, and the first sparstencil_run
+ *            times two sweeps of every depth up to it on its own input (after one warm-up
+ *            sweep each; that call synchronises its stream once) and keeps the depth with the
+ *            least time per step.  sparstencil_query reports the planned maximum until then.
  *   out_plan: receives the plan (owned by the library until sparstencil_plan_destroy).
  * Host only (no device work).  Errors: SPST_ERR_INVALID, SPST_ERR_UNSUPPORTED
  * (ndim not 2/3, radius too large for TMEM, ...), SPST_ERR_NOMEM.
@@ -143,9 +146,14 @@ size_t sparstencil_workspace_bytes(sparstencil_plan_t plan);
 sparstencil_status sparstencil_bind_workspace(sparstencil_plan_t plan, void* dev, size_t bytes,
                                               cudaStream_t stream);
 
-/* Runs n independent jobs (plans[i] on in[i] -> out[i] for steps[i] steps) on `stream`.
- * Plans must be distinct.  Jobs are interleaved sweep by sweep so that the sweeps of
- * different grids overlap on the device. */
+/* Runs n independent jobs (plans[i] on in[i] -> out[i] for steps[i] steps) as one CUDA
+ * graph launched on `stream`: job i's copy-in and sweeps form branch i mod 16 of the graph,
+ * and the branches run side by side on the device (many small grids share the SMs).  Plans
+ * must be distinct.  Before capturing, the call prepares every plan (workspace, the
+ * fusion-depth search of fusion_depth-0 plans, device tables) and synchronises `stream`;
+ * the graph itself is launched asynchronously.  Results equal those of sparstencil_run on
+ * each job (same plans, same kernels).  Errors as sparstencil_run, plus SPST_ERR_INVALID
+ * for repeated plans. */
 sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const float* const* in,
                                          float* const* out, const int64_t* steps, int n, cudaStream_t stream);
 
@@ -158,7 +166,9 @@ sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_i
  *   order:      kpad ints, original column of A' per permuted K position, -1 = zero column
  *   a_hi, a_lo: 128 * kpad/2 floats, compressed A'' values: a_hi is the first 16-bit piece
  *               of each weight, a_lo the sum of its remaining pieces (single-word modes keep
- *               two pieces, split modes three; for BF16 split a_hi + a_lo is the FP32 weight)
+ *               two pieces, split modes three, or two for a fused sweep whose three pieces
+ *               would leave TMEM room for only one accumulator; with three BF16 pieces
+ *               a_hi + a_lo is the FP32 weight)
  *   a_idx:      128 * kpad/2 bytes, in-group position (0..3) of each compressed value
  *   lut:        kpad ints, tile-word offset gathered for each permuted K position
  *   fused_w:    (2tr+1)^ndim doubles, the composed weights of the sweep

@@ -95,6 +95,7 @@ struct sparstencil_plan_s {
   sparstencil_dtype dtype;
   sparstencil_boundary bc;
   int requested_t = 1, t = 1, t_max = 1;
+  bool autotune_pending = false;  // fusion_depth 0: t is chosen by timing at the first run
   std::vector<double> w64;  // input weights (FP32 values promoted exactly)
   PlanGeometry geo;
   SweepTables full;
@@ -147,6 +148,25 @@ std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
   }
   out->t = depth;
   if (tmem_accumulators(*out) == 0) return "stencil too wide for TMEM (kpad " + std::to_string(out->kpad) + ")";
+  return "";
+}
+
+// Geometry of the padded ping-pong grids and halo tiles for ghost width t_max * radius;
+// returns an empty string or the reason the grid cannot be planned.
+std::string plan_geometry(sparstencil_plan_t p) {
+  PlanGeometry& g = p->geo;
+  g.G = p->t_max * p->radius;
+  if (g.G > 60) return "fused radius too large";
+  if (g.H < 2 * g.G || g.W < 2 * g.G || g.W < 4) return "grid smaller than twice the fused radius";
+  if (g.H > (1 << 30) || g.W > (1 << 30)) return "grid extent too large";
+  g.Hp = g.H + 2 * g.G;
+  g.Wp = ((g.W + 2 * g.G) + 3) / 4 * 4;
+  g.P = (Tile2D::TX + 2 * g.G + 3) / 4 * 4;
+  g.box_h = Tile2D::TY + 2 * g.G;
+  g.tiles_x = (g.W + Tile2D::TX - 1) / Tile2D::TX;
+  g.tiles_y = (g.H + Tile2D::TY - 1) / Tile2D::TY;
+  g.num_tiles = g.tiles_x * g.tiles_y;
+  if (g.num_tiles > (1ll << 30)) return "too many tiles";
   return "";
 }
 
@@ -262,6 +282,117 @@ struct LaunchTimer {
   }
 };
 
+// Launch parameters of a sweep of depth T.depth that depend only on the plan and the tables.
+spst::Sweep2DParams sweep_params(sparstencil_plan_t p, const SweepTables& T, const DeviceTables& dt, int* status) {
+  const PlanGeometry& g = p->geo;
+  spst::Sweep2DParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.H = (int)g.H;
+  prm.W = (int)g.W;
+  prm.G = g.G;
+  prm.tiles_x = (int)g.tiles_x;
+  prm.tiles_y = (int)g.tiles_y;
+  prm.num_tiles = (int)g.num_tiles;
+  prm.P = g.P;
+  prm.box_h = g.box_h;
+  prm.kpad = T.kpad;
+  prm.kchunks = T.kpad / 32;
+  prm.a_pieces = T.a_pieces;
+  prm.b_pieces = is_split(p->dtype) ? 2 : 1;
+  prm.nterms = 0;
+  prm.term_a[prm.nterms] = 0;
+  prm.term_b[prm.nterms++] = 0;
+  if (prm.b_pieces == 2) {
+    prm.term_a[prm.nterms] = 0;
+    prm.term_b[prm.nterms++] = 1;
+  }
+  for (int pc = 1; pc < T.a_pieces; pc++) {
+    prm.term_a[prm.nterms] = pc;
+    prm.term_b[prm.nterms++] = 0;
+  }
+  prm.nacc = tmem_accumulators(T);
+  prm.fp16 = word_of(p->dtype) == spst::Word::FP16 ? 1 : 0;
+  prm.wscale = std::ldexp(1.0f, -T.wscale_log2);
+  prm.lut = dt.lut;
+  prm.a_words = dt.a_words;
+  prm.meta_words = dt.meta;
+  prm.S_hi = T.S_hi;
+  prm.S_lo = T.S_lo;
+  prm.status = status;
+  prm.wait_ns = g_wait_ns;
+  return prm;
+}
+
+// Fusion-depth search of a plan made with fusion_depth 0 (the layout search of Sec. 3.3,
+// done by measurement): copies `in` into the padded grid, times two sweeps of every
+// candidate depth after one warm-up sweep, and keeps the depth with the least time per time
+// step.  Synchronises the stream; the caller's run then starts from a fresh copy-in.
+sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStream_t stream) {
+  const PlanGeometry& g = p->geo;
+  int* status = spst::device_status_word();
+  if (!status) return fail(SPST_ERR_CUDA, "device status word unavailable");
+  SPST_CUDA(spst::launch_pad_copy2d(in, p->pad(0), (int)g.H, (int)g.W, g.G, g.Wp, p->bc == SPST_PERIODIC ? 1 : 0,
+                                    stream),
+            "pad copy");
+  cudaEvent_t e0, e1;
+  SPST_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(SPST_ERR_CUDA, "cudaEventCreate");
+  }
+  int best = p->t;
+  double best_ms = 1e300;
+  sparstencil_status s = SPST_OK;
+  for (int depth = 1; depth <= p->t_max && s == SPST_OK; depth++) {
+    std::string err;
+    const SweepTables* T = tables_for(p, depth, &err);
+    if (!T) continue;
+    DeviceTables* dt = nullptr;
+    if ((s = ensure_device_tables(p, depth, *T, &dt)) != SPST_OK) break;
+    int cur = 0;
+    float ms = 0.f;
+    for (int k = 0; k < 3 && s == SPST_OK; k++) {
+      if (k == 1 && cudaEventRecord(e0, stream) != cudaSuccess) s = fail(SPST_ERR_CUDA, "cudaEventRecord");
+      spst::Sweep2DParams prm = sweep_params(p, *T, *dt, status);
+      prm.out = p->pad(1 - cur);
+      prm.out_pitch = g.Wp;
+      prm.out_off = g.G;
+      prm.out_ghost = p->bc == SPST_PERIODIC ? 1 : 0;
+      if (spst::launch_sweep2d(p->tmap[cur], prm, p->num_sms, stream) != cudaSuccess ||
+          launch_band(p, depth, p->pad(cur), prm.out, prm.out_pitch, prm.out_off, stream) != cudaSuccess)
+        s = fail(SPST_ERR_CUDA, "autotune sweep launch");
+      cur = 1 - cur;
+    }
+    if (s != SPST_OK) break;
+    if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      s = fail(SPST_ERR_CUDA, "autotune timing");
+      break;
+    }
+    const double per_step = (double)ms / (2.0 * depth);
+    if (per_step < best_ms) {
+      best_ms = per_step;
+      best = depth;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != SPST_OK) return s;
+  if (best != p->t) {
+    std::string err;
+    const SweepTables* T = tables_for(p, best, &err);
+    if (!T) return fail(SPST_ERR_UNSUPPORTED, err);
+    SweepTables chosen = *T;
+    p->rem[p->t] = std::move(p->full);
+    p->full = std::move(chosen);
+    p->rem.erase(best);
+    // device tables are keyed by depth and stay valid
+    p->t = best;
+  }
+  p->autotune_pending = false;
+  return SPST_OK;
+}
+
 sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out, int64_t T, cudaStream_t stream,
                               LaunchTimer* timer = nullptr) {
   sparstencil_status s = ensure_device(p, stream);
@@ -271,6 +402,7 @@ sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out,
     SPST_CUDA(cudaMemcpyAsync(out, in, (size_t)g.H * g.W * 4, cudaMemcpyDeviceToDevice, stream), "copy in->out");
     return SPST_OK;
   }
+  if (p->autotune_pending && (s = autotune_depth(p, in, stream)) != SPST_OK) return s;
   std::vector<int> sweeps((size_t)(T / p->t), p->t);
   if (T % p->t) sweeps.push_back((int)(T % p->t));
   int* status = spst::device_status_word();
@@ -294,47 +426,12 @@ sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out,
   if (timer && (s = timer->record(stream)) != SPST_OK) return s;
   int cur = 0;
   for (size_t i = 0; i < sweeps.size(); i++) {
-    const SweepTables* T_ = tabs[i];
-    DeviceTables* dt = dtabs[i];
     const bool last = (i + 1 == sweeps.size());
-    spst::Sweep2DParams prm;
-    prm.H = (int)g.H;
-    prm.W = (int)g.W;
-    prm.G = g.G;
-    prm.tiles_x = (int)g.tiles_x;
-    prm.tiles_y = (int)g.tiles_y;
-    prm.num_tiles = (int)g.num_tiles;
-    prm.P = g.P;
-    prm.box_h = g.box_h;
-    prm.kpad = T_->kpad;
-    prm.kchunks = T_->kpad / 32;
-    prm.a_pieces = T_->a_pieces;
-    prm.b_pieces = is_split(p->dtype) ? 2 : 1;
-    prm.nterms = 0;
-    prm.term_a[prm.nterms] = 0;
-    prm.term_b[prm.nterms++] = 0;
-    if (prm.b_pieces == 2) {
-      prm.term_a[prm.nterms] = 0;
-      prm.term_b[prm.nterms++] = 1;
-    }
-    for (int pc = 1; pc < T_->a_pieces; pc++) {
-      prm.term_a[prm.nterms] = pc;
-      prm.term_b[prm.nterms++] = 0;
-    }
-    prm.nacc = tmem_accumulators(*T_);
-    prm.fp16 = word_of(p->dtype) == spst::Word::FP16 ? 1 : 0;
-    prm.wscale = std::ldexp(1.0f, -T_->wscale_log2);
-    prm.lut = dt->lut;
-    prm.a_words = dt->a_words;
-    prm.meta_words = dt->meta;
-    prm.S_hi = T_->S_hi;
-    prm.S_lo = T_->S_lo;
+    spst::Sweep2DParams prm = sweep_params(p, *tabs[i], *dtabs[i], status);
     prm.out = last ? out : p->pad(1 - cur);
     prm.out_pitch = last ? g.W : g.Wp;
     prm.out_off = last ? 0 : g.G;
     prm.out_ghost = (!last && p->bc == SPST_PERIODIC) ? 1 : 0;
-    prm.status = status;
-    prm.wait_ns = g_wait_ns;
     SPST_CUDA(spst::launch_sweep2d(p->tmap[cur], prm, p->num_sms, stream), "sweep launch");
     SPST_CUDA(launch_band(p, sweeps[i], p->pad(cur), prm.out, prm.out_pitch, prm.out_off, stream), "band launch");
     cur = 1 - cur;
@@ -459,41 +556,12 @@ sparstencil_status run_plan_with_buffers(sparstencil_plan_t p, const float* in, 
     const Region* rg = nullptr;
     for (int r = 0; r < nreg; r++)
       if (regions[r].depth == sweeps[i]) rg = &regions[r];
-    const SweepTables* T_ = rg->T;
     const bool last = (i + 1 == sweeps.size());
-    Sweep2DParams prm;
-    std::memset(&prm, 0, sizeof(prm));
-    prm.H = (int)g.H;
-    prm.W = (int)g.W;
-    prm.G = g.G;
-    prm.tiles_x = (int)g.tiles_x;
-    prm.tiles_y = (int)g.tiles_y;
-    prm.num_tiles = (int)g.num_tiles;
-    prm.P = g.P;
-    prm.box_h = g.box_h;
-    prm.kpad = T_->kpad;
-    prm.kchunks = T_->kpad / 32;
-    prm.a_pieces = T_->a_pieces;
-    prm.b_pieces = is_split(p->dtype) ? 2 : 1;
-    prm.nterms = 0;
-    prm.term_a[prm.nterms] = 0;
-    prm.term_b[prm.nterms++] = 0;
-    if (prm.b_pieces == 2) {
-      prm.term_a[prm.nterms] = 0;
-      prm.term_b[prm.nterms++] = 1;
-    }
-    for (int pc = 1; pc < T_->a_pieces; pc++) {
-      prm.term_a[prm.nterms] = pc;
-      prm.term_b[prm.nterms++] = 0;
-    }
-    prm.nacc = tmem_accumulators(*T_);
-    prm.fp16 = word_of(p->dtype) == Word::FP16 ? 1 : 0;
-    prm.wscale = std::ldexp(1.0f, -T_->wscale_log2);
-    prm.lut = rg->lut;
-    prm.a_words = rg->a_words;
-    prm.meta_words = rg->meta;
-    prm.S_hi = T_->S_hi;
-    prm.S_lo = T_->S_lo;
+    DeviceTables dtv;
+    dtv.lut = rg->lut;
+    dtv.a_words = rg->a_words;
+    dtv.meta = rg->meta;
+    Sweep2DParams prm = sweep_params(p, *rg->T, dtv, status);  // dtv borrows the static tables
     prm.out = last ? out : pad[1 - cur];
     prm.out_pitch = last ? g.W : g.Wp;
     prm.out_off = last ? 0 : g.G;
@@ -549,6 +617,9 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   if (bc == SPST_DIRICHLET_ZERO && p->t > 1 && radius > 4)
     return fail(SPST_ERR_UNSUPPORTED, "temporal fusion with a Dirichlet boundary needs radius <= 4");
   p->t_max = p->t;
+  // fusion_depth 0: the deepest of 3, 2, 1 whose tables fit is planned; the first run times
+  // every depth up to it and keeps the fastest per time step
+  const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && radius > 4) ? 1 : 3) : p->t;
   const int side = 2 * radius + 1;
   p->w64.resize((size_t)side * side);
   for (size_t i = 0; i < p->w64.size(); i++) p->w64[i] = (double)weights[i];
@@ -556,33 +627,26 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   g.ndim = 2;
   g.H = dims[0];
   g.W = dims[1];
-  g.G = p->t_max * radius;
-  if (g.G > 60) return fail(SPST_ERR_UNSUPPORTED, "fused radius too large");
-  if (g.H < 2 * g.G || g.W < 2 * g.G || g.W < 4)
-    return fail(SPST_ERR_UNSUPPORTED, "grid smaller than twice the fused radius");
-  if (g.H > (1 << 30) || g.W > (1 << 30)) return fail(SPST_ERR_UNSUPPORTED, "grid extent too large");
-  g.Hp = g.H + 2 * g.G;
-  g.Wp = ((g.W + 2 * g.G) + 3) / 4 * 4;
-  g.P = (Tile2D::TX + 2 * g.G + 3) / 4 * 4;
-  g.box_h = Tile2D::TY + 2 * g.G;
-  g.tiles_x = (g.W + Tile2D::TX - 1) / Tile2D::TX;
-  g.tiles_y = (g.H + Tile2D::TY - 1) / Tile2D::TY;
-  g.num_tiles = g.tiles_x * g.tiles_y;
-  if (g.num_tiles > (1ll << 30)) return fail(SPST_ERR_UNSUPPORTED, "too many tiles");
-  std::string err = build_tables(p.get(), p->t, &p->full);
-  if (!err.empty()) return fail(SPST_ERR_UNSUPPORTED, err);
-  {
-    spst::Sweep2DParams probe;
-    std::memset(&probe, 0, sizeof(probe));
-    probe.P = g.P;
-    probe.box_h = g.box_h;
-    probe.kpad = p->full.kpad;
-    probe.kchunks = p->full.kpad / 32;
-    probe.a_pieces = p->full.a_pieces;
-    probe.b_pieces = is_split(dtype) ? 2 : 1;
-    if (!spst::sweep2d_fits(probe))
-      return fail(SPST_ERR_UNSUPPORTED, "halo tile of the fused radius does not fit in shared memory");
+  std::string err;
+  for (int tm = t_try; tm >= 1; tm--) {
+    p->t = p->t_max = tm;
+    err = plan_geometry(p.get());
+    if (err.empty()) err = build_tables(p.get(), p->t, &p->full);
+    if (err.empty()) {
+      spst::Sweep2DParams probe;
+      std::memset(&probe, 0, sizeof(probe));
+      probe.P = g.P;
+      probe.box_h = g.box_h;
+      probe.kpad = p->full.kpad;
+      probe.kchunks = p->full.kpad / 32;
+      probe.a_pieces = p->full.a_pieces;
+      probe.b_pieces = is_split(dtype) ? 2 : 1;
+      if (!spst::sweep2d_fits(probe)) err = "halo tile of the fused radius does not fit in shared memory";
+    }
+    if (err.empty() || fusion_depth != 0) break;
   }
+  if (!err.empty()) return fail(SPST_ERR_UNSUPPORTED, err);
+  p->autotune_pending = fusion_depth == 0 && p->t_max > 1;
   p->planner_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out_plan = p.release();
   return SPST_OK;
@@ -670,11 +734,80 @@ sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in
 sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const float* const* in, float* const* out,
                                          const int64_t* steps, int n, cudaStream_t stream) {
   if (n < 0 || (n > 0 && (!plans || !in || !out || !steps))) return fail(SPST_ERR_INVALID, "bad batch arguments");
+  if (n == 0) return SPST_OK;
   for (int i = 0; i < n; i++) {
-    sparstencil_status s = sparstencil_run(plans[i], in[i], out[i], steps[i], stream);
-    if (s != SPST_OK) return s;
+    if (!plans[i] || !in[i] || !out[i]) return fail(SPST_ERR_INVALID, "null plan or grid in the batch");
+    if (steps[i] < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
+    if (in[i] == out[i]) return fail(SPST_ERR_INVALID, "in and out must not alias");
+    for (int j = 0; j < i; j++)
+      if (plans[j] == plans[i]) return fail(SPST_ERR_INVALID, "plans in a batch must be distinct");
   }
-  return SPST_OK;
+  // Everything that allocates, uploads or synchronises happens before the capture: device
+  // state, the fusion-depth search of autotuned plans, and the tables of every sweep depth.
+  for (int i = 0; i < n; i++) {
+    sparstencil_plan_t p = plans[i];
+    sparstencil_status s = ensure_device(p, stream);
+    if (s != SPST_OK) return s;
+    if (steps[i] > 0 && p->autotune_pending && (s = autotune_depth(p, in[i], stream)) != SPST_OK) return s;
+    const int depths[2] = {p->t, (int)(steps[i] % p->t)};
+    for (int d : depths) {
+      if (d <= 0 || steps[i] == 0) continue;
+      std::string err;
+      const SweepTables* T = tables_for(p, d, &err);
+      if (!T) return fail(SPST_ERR_UNSUPPORTED, err);
+      DeviceTables* dt = nullptr;
+      if ((s = ensure_device_tables(p, d, *T, &dt)) != SPST_OK) return s;
+    }
+  }
+  SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
+  // One CUDA graph: job i runs on branch i mod nb, the branches run side by side.
+  const int nb = n < 16 ? n : 16;
+  std::vector<cudaStream_t> br(nb, nullptr);
+  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  sparstencil_status s = SPST_OK;
+  auto cleanup = [&]() {
+    spst::sweep2d_set_programmatic_launch(true);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+    for (auto b : br)
+      if (b) cudaStreamDestroy(b);
+    if (cap) cudaStreamDestroy(cap);
+  };
+  auto cuda_ok = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && s == SPST_OK) s = cuda_fail(e, what);
+    return s == SPST_OK;
+  };
+  if (!cuda_ok(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create capture stream")) {
+    cleanup();
+    return s;
+  }
+  for (int b = 0; b < nb && s == SPST_OK; b++) cuda_ok(cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking), "create branch stream");
+  for (int e = 0; e <= nb && s == SPST_OK; e++) cuda_ok(cudaEventCreateWithFlags(&ev[e], cudaEventDisableTiming), "create event");
+  if (s != SPST_OK) {
+    cleanup();
+    return s;
+  }
+  spst::sweep2d_set_programmatic_launch(false);  // plain stream order inside the graph
+  if (cuda_ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture")) {
+    cuda_ok(cudaEventRecord(ev[nb], cap), "fork event");
+    for (int b = 0; b < nb && s == SPST_OK; b++) cuda_ok(cudaStreamWaitEvent(br[b], ev[nb], 0), "fork wait");
+    for (int i = 0; i < n && s == SPST_OK; i++) s = run_sweeps(plans[i], in[i], out[i], steps[i], br[i % nb]);
+    for (int b = 0; b < nb && s == SPST_OK; b++) {
+      cuda_ok(cudaEventRecord(ev[b], br[b]), "join event");
+      cuda_ok(cudaStreamWaitEvent(cap, ev[b], 0), "join wait");
+    }
+    const cudaError_t ee = cudaStreamEndCapture(cap, &graph);  // always ends the capture
+    cuda_ok(ee, "end capture");
+  }
+  if (s == SPST_OK && cuda_ok(cudaGraphInstantiate(&exec, graph, 0), "instantiate batch graph"))
+    cuda_ok(cudaGraphLaunch(exec, stream), "launch batch graph");
+  cleanup();  // the launched graph keeps its own copy of the work
+  return s;
 }
 
 sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_info* info) {

@@ -54,6 +54,9 @@ int sweep2d_max_slots(const Sweep2DParams& p);
 // Whether the sweep kernel fits shared memory for this geometry (halo stages, >= 2 chunk
 // slots, and the set-up staging of A'' and the metadata).
 bool sweep2d_fits(const Sweep2DParams& p);
+// Whether launch_sweep2d lets a sweep overlap its set-up with the previous kernel
+// (programmatic dependent launch; on by default, per host thread).
+void sweep2d_set_programmatic_launch(bool on);
 // Launches one sparse sweep (grid = min(num_tiles, SMs)); returns the launch error.
 cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p, int num_sms, cudaStream_t stream);
 

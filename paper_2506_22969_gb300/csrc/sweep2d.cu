@@ -770,6 +770,11 @@ bool sweep2d_fits(const Sweep2DParams& p_in) {
   return staging_bytes(p) <= (size_t)SmemLayout(p).off_lut;
 }
 
+namespace {
+thread_local bool t_pdl = true;
+}
+void sweep2d_set_programmatic_launch(bool on) { t_pdl = on; }
+
 cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p_in, int num_sms, cudaStream_t stream) {
   Sweep2DParams p = p_in;
   p.nslots = sweep2d_max_slots(p);
@@ -796,7 +801,7 @@ cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p_in
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = t_pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, tmap_in, p);
 }
 

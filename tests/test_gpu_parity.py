@@ -83,6 +83,26 @@ def test_zero_and_one_step(torch_cuda, oracle_mod):
     assert oracle_mod.rel_errors(got1, oracle_mod.run(u, w, "periodic", 1))[0] <= 1e-5
 
 
+def test_autotuned_depth_matches_oracle(torch_cuda, oracle_mod):
+    """fusion_depth 0: the first run picks a depth by timing; results meet the split
+    tolerance and a second run with the chosen depth repeats the first bit for bit."""
+    torch = torch_cuda
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=4)
+    u = inputs.uniform01(9, (300, 260))
+    plan = binding.Plan(w, u.shape, dtype="bf16_split", bc="periodic", fusion_depth=0)
+    x = torch.from_numpy(u).cuda()
+    y1 = torch.empty_like(x)
+    y2 = torch.empty_like(x)
+    plan.run(x, y1, 20)
+    t = plan.info().fusion_depth
+    assert t in (1, 2, 3)
+    plan.run(x, y2, 20)
+    assert binding.device_status() == 0
+    assert torch.equal(y1, y2)
+    ref = oracle_mod.run(u, w, "periodic", 20)
+    assert oracle_mod.rel_errors(y1.cpu().numpy().astype(np.float64), ref)[0] <= 1e-5
+
+
 def test_closed_form_fourier_mode(torch_cuda):
     """Periodic closed form, no oracle: u0 = 1/2 + 1/2 cos(theta.x) evolves to
     1/2 S^T + 1/2 Re(lambda^T e^{i theta.x}), S = sum w, lambda = sum_o w[o] e^{i theta.o};
@@ -202,3 +222,34 @@ def test_bounded_wait_reports_timeout(torch_cuda):
         binding.set_wait_limit_ns(0)
     plan.run(x, y, 2)
     assert binding.device_status() == 0
+
+
+def test_batch_graph_equals_individual_runs(torch_cuda):
+    """sparstencil_run_batch (one CUDA graph, jobs side by side) gives each job exactly the
+    result of sparstencil_run on its own: mixed sizes, stencils, precisions, boundaries and
+    step counts, including a zero-step job and an autotuned plan."""
+    torch = torch_cuda
+    jobs = [("star", 3, "gaussian", (256, 384), 7, "periodic", "bf16", 1),
+            ("box", 3, "gaussian", (384, 256), 5, "periodic", "bf16_split", 1),
+            ("box", 1, "random", (200, 136), 10, "dirichlet", "bf16_split", 3),
+            ("star", 1, "heat", (512, 512), 8, "dirichlet", "fp16", 1),
+            ("box", 2, "random", (300, 260), 0, "periodic", "bf16", 1),
+            ("box", 1, "random", (260, 300), 9, "periodic", "bf16_split", 0)]
+    plans, xs, alone, outs, steps = [], [], [], [], []
+    for k, (shape, r, recipe, dims, T, bc, dtype, t) in enumerate(jobs):
+        w = inputs.stencil_weights(shape, 2, r, recipe, seed=20 + k)
+        u = inputs.uniform01(30 + k, dims)
+        x = torch.from_numpy(u).cuda()
+        plan = binding.Plan(w, dims, dtype=dtype, bc=bc, fusion_depth=t, shape=shape)
+        y = torch.empty_like(x)
+        plan.run(x, y, T)  # alone (an autotuned plan fixes its depth here)
+        plans.append(plan)
+        xs.append(x)
+        alone.append(y)
+        outs.append(torch.full_like(x, float("nan")))
+        steps.append(T)
+    binding.run_batch(plans, xs, outs, steps)
+    torch.cuda.synchronize()
+    assert binding.device_status() == 0
+    for a, b in zip(alone, outs):
+        assert torch.equal(a, b)

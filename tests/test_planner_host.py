@@ -232,3 +232,14 @@ def test_cost_model_orders_layouts():
     trans1 = kp1 * (mp1 / 2 + np1)
     trans2 = kp2 * (mp2 / 2 + np2)
     assert trans2 < trans1 / 5
+
+
+def test_autotune_plan_takes_the_deepest_depth_that_fits(lib):
+    """fusion_depth 0 plans the deepest of 3, 2, 1 whose tables fit (the first run then
+    times each depth up to it)."""
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
+    p = binding.Plan(w, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=0)
+    assert p.info().fusion_depth == 3 and p.info().ghost == 3
+    w3 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=2)
+    p3 = binding.Plan(w3, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=0)
+    assert p3.info().fusion_depth == 1
