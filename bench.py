@@ -261,7 +261,16 @@ def main():
     ap.add_argument("--ncu-case", default=None,
                     help="profiling case for ncu: '<precision>:<side>' runs a few single sweeps of Box-2D9P "
                          "on a side x side periodic grid and exits (no JSON line)")
+    ap.add_argument("--suite", action="store_true", help="configs C1, C3, C4a/b (one JSON line each) and exit")
+    ap.add_argument("--batch", action="store_true", help="config C4c (64 grids in one CUDA graph) and exit")
+    ap.add_argument("--serve", action="store_true", help="config C5 (Poisson-arrival job server) and exit")
     args = ap.parse_args()
+    if args.suite:
+        return suite_mode()
+    if args.batch:
+        return batch_mode()
+    if args.serve:
+        return serve_mode()
     if args.impl == "reference":
         return run_reference(args)
     if args.ncu_case:
@@ -437,6 +446,252 @@ def main():
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+# Extra workloads (not the driver's JSON line): --suite, --batch, --serve print one JSON
+# line per workload on stdout.
+# ---------------------------------------------------------------------------------------
+def _time_runs(fn, k=3, warm=1, flush=None):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(k):
+        if flush is not None:
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return min(ts), statistics.median(ts)
+
+
+def _rel_l2_gpu(binding, x, ref):
+    l2, linf, _ = binding.error_norms(x, ref)
+    return l2, linf
+
+
+def suite_mode():
+    """Configs C1, C3, C4a/b: GStencil/s of the sparse path (single and split, fusion depth
+    autotuned) and of the plain FP32 direct kernel, with rel-L2 against the FP64 oracle (C1:
+    full grid; C3: sampled points) or against the FP32 direct result (C4)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2506_22969_gb300 import binding, inputs
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for name in ("heat2d_512", "star2d13p_8192", "box2d49p_8192", "box3d27p_256", "heat3d_512"):
+        cfg = inputs.CONFIGS[name]
+        dims, T, bc = cfg["dims"], cfg["steps"], cfg["bc"]
+        w = inputs.stencil_weights(cfg["shape"], cfg["ndim"], cfg["radius"], cfg["recipe"], seed=cfg["seed"])
+        u = inputs.make_grid(cfg["grid"], cfg["seed"], dims)
+        x = torch.from_numpy(u).cuda()
+        y = torch.empty_like(x)
+        work = torch.empty_like(x)
+        pts = T * int(np.prod(dims))
+        line = {"workload": cfg["name"], "points": list(dims), "steps": T}
+        ref_gpu = torch.empty_like(x)
+        ms_d, _ = _time_runs(lambda: binding.direct_run(w, x, ref_gpu, work, T, bc=bc), 2, 1, flush)
+        line["fp32_direct_gstencil_s"] = pts / ms_d / 1e6
+        if cfg["ndim"] == 3:
+            rng = np.random.default_rng(0)
+            sample = [tuple(int(rng.integers(0, d)) for d in dims) for _ in range(6)]
+            ref = np.array([oracle.point(u, w, bc, T, p) for p in sample])
+            got = ref_gpu.cpu().numpy().astype(np.float64)
+            vals = np.array([got[p] for p in sample])
+            line["fp32_direct_rel_l2_sampled_vs_oracle"] = float(np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2)))
+            line["sparse"] = "not built for 3D grids (FP32 CUDA-core kernel only)"
+            print(json.dumps(line), flush=True)
+            continue
+        dtypes = ("fp16",) if name == "heat2d_512" else ("bf16", "bf16_split")
+        full_ref = oracle.run(u, w, bc, T) if name == "heat2d_512" else None
+        for dt in dtypes:
+            try:
+                plan = binding.Plan(w, dims, dtype=dt, bc=bc, fusion_depth=0, shape=cfg["shape"])
+            except binding.SparStencilError as e:
+                line[f"{dt}_sparse"] = f"unsupported: {e}"
+                continue
+            plan.run(x, y, T)  # fixes the autotuned depth
+            ms, med = _time_runs(lambda: plan.run(x, y, T), 3, 1, flush)
+            line[f"{dt}_sparse_gstencil_s"] = pts / ms / 1e6
+            line[f"{dt}_fusion_depth"] = plan.info().fusion_depth
+            if full_ref is not None:
+                l2, linf = oracle.rel_errors(y.cpu().numpy().astype(np.float64), full_ref)
+                line[f"{dt}_rel_l2_vs_oracle"] = l2
+                line[f"{dt}_rel_linf_vs_oracle"] = linf
+            else:
+                l2, linf = _rel_l2_gpu(binding, y, ref_gpu)
+                line[f"{dt}_rel_l2_vs_fp32_direct"] = l2
+                line[f"{dt}_rel_linf_vs_fp32_direct"] = linf
+        print(json.dumps(line), flush=True)
+        del x, y, work, ref_gpu
+        torch.cuda.empty_cache()
+
+
+def _c4c_jobs(n=64, seed=4):
+    """64 grids, side log-uniform in [256, 2048] rounded to 128, alternating Star-2D13P and
+    Box-2D49P (Gaussian weights), 200 steps, periodic."""
+    from paper_2506_22969_gb300 import inputs
+    z = inputs.uniform01(seed, (n,)).astype(np.float64)
+    sides = np.exp(np.log(256) + z * (np.log(2048) - np.log(256)))
+    sides = (np.round(sides / 128) * 128).astype(int)
+    jobs = []
+    for i in range(n):
+        shape = "star" if i % 2 == 0 else "box"
+        w = inputs.stencil_weights(shape, 2, 3, "gaussian", seed=seed)
+        jobs.append((shape, w, (int(sides[i]), int(sides[i])), 200))
+    return jobs
+
+
+def batch_mode():
+    """Config C4c: 64 mixed grids in one CUDA graph (sparstencil_run_batch) against the same
+    jobs run one after another; per-grid rel-L2 against the FP32 direct kernel."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_22969_gb300 import binding, inputs
+    jobs = _c4c_jobs()
+    plans, xs, ys = [], [], []
+    for k, (shape, w, dims, T) in enumerate(jobs):
+        u = inputs.uniform01(100 + k, dims)
+        plans.append(binding.Plan(w, dims, dtype="bf16", bc="periodic", fusion_depth=0, shape=shape))
+        xs.append(torch.from_numpy(u).cuda())
+        ys.append(torch.empty(dims, device="cuda"))
+    steps = [j[3] for j in jobs]
+    pts = sum(T * d[0] * d[1] for (_, _, d, T) in jobs)
+    ms_b, med_b = _time_runs(lambda: binding.run_batch(plans, xs, ys, steps), 3, 1)
+    ms_s, _ = _time_runs(lambda: [p.run(x, y, T) for p, x, y, T in zip(plans, xs, ys, steps)], 3, 1)
+    worst = 0.0
+    for (shape, w, dims, T), x, y in zip(jobs, xs, ys):
+        ref = torch.empty_like(x)
+        work = torch.empty_like(x)
+        binding.direct_run(w, x, ref, work, T, bc="periodic")
+        worst = max(worst, _rel_l2_gpu(binding, y, ref)[0])
+    print(json.dumps({"workload": "C4c: 64 grids 256^2-2048^2, Star-2D13P / Box-2D49P alternating, 200 steps, BF16",
+                      "grids": len(jobs), "point_steps": pts, "graph_ms": ms_b, "graph_gstencil_s": pts / ms_b / 1e6,
+                      "sequential_ms": ms_s, "sequential_gstencil_s": pts / ms_s / 1e6,
+                      "worst_rel_l2_vs_fp32_direct": worst,
+                      "depths": sorted({p.info().fusion_depth for p in plans})}), flush=True)
+
+
+def _c5_jobs(n=512, seed=5):
+    """Config C5: stencil uniform over 5/9/13/49-point 2D and 7/27-point 3D; 2D side
+    log-uniform 128-4096, 3D side 64-256 (multiples of 8); steps uniform in [10, 500];
+    tolerance class 2e-3 (single-word BF16) or 1e-5 (split BF16) with probability 1/2."""
+    from paper_2506_22969_gb300 import inputs
+    r = inputs.uniform01(seed, (n, 4)).astype(np.float64)
+    kinds = [("star", 2, 1, "heat"), ("box", 2, 1, "random"), ("star", 2, 3, "gaussian"), ("box", 2, 3, "gaussian"),
+             ("star", 3, 1, "random"), ("box", 3, 1, "random")]
+    jobs = []
+    for i in range(n):
+        shape, nd, rad, recipe = kinds[min(5, int(r[i, 0] * 6))]
+        lo, hi = (128, 4096) if nd == 2 else (64, 256)
+        side = int(np.exp(np.log(lo) + r[i, 1] * (np.log(hi) - np.log(lo))) // 8 * 8)
+        dims = (side,) * nd
+        T = 10 + int(r[i, 2] * 491)
+        dtype = "bf16_split" if r[i, 3] < 0.5 else "bf16"
+        w = inputs.stencil_weights(shape, nd, rad, recipe, seed=seed + i % 3)
+        fusion = 1 if (rad == 3 and dtype == "bf16_split") else (3 if rad == 1 else 1)
+        jobs.append(dict(shape=shape, w=w, dims=dims, T=T, dtype=dtype, fusion=fusion))
+    return jobs
+
+
+def serve_mode(n_jobs=512, budget=120 << 30, slots=8):
+    """Config C5: Poisson arrivals at 0.8 of the measured capacity into the library's job
+    server (HBM budget 120 GB, 8 slots); p50/p99 of completion minus arrival, throughput, and a
+    sample of jobs re-run alone (bit-exact equality with their result in the mix)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_22969_gb300 import binding, inputs
+    jobs = _c5_jobs(n_jobs)
+    base2 = inputs.uniform01(5, (4096, 4096))
+    base3 = inputs.uniform01(6, (256, 256, 256))
+    npool = 3 * slots
+    pool_in = [torch.empty(4096 * 4096, dtype=torch.float32).pin_memory() for _ in range(npool)]
+    pool_out = [torch.empty(4096 * 4096, dtype=torch.float32).pin_memory() for _ in range(npool)]
+
+    def grid_of(j):
+        d = j["dims"]
+        return base2[:d[0], :d[1]] if len(d) == 2 else base3[:d[0], :d[1], :d[2]]
+
+    keep = set(range(0, n_jobs, 37))  # jobs whose results are re-checked alone
+
+    def run_trace(srv, idx, arrivals):
+        free = list(range(npool))
+        inflight = {}
+        t0 = srv.clock()
+        results = {}
+        for k, i in enumerate(idx):
+            j = jobs[i]
+            while not free:  # wait for a buffer pair (backpressure only when far over capacity)
+                jid, (bi, ii) = next(iter(inflight.items()))
+                srv.wait(jid)
+                if ii in keep:
+                    results[ii] = pool_out[bi][:int(np.prod(jobs[ii]["dims"]))].clone()
+                free.append(bi)
+                del inflight[jid]
+            bi = free.pop()
+            size = int(np.prod(j["dims"]))
+            hin = pool_in[bi][:size].view(*j["dims"])
+            hin.copy_(torch.from_numpy(np.ascontiguousarray(grid_of(j))))
+            hout = pool_out[bi][:size].view(*j["dims"])
+            while srv.clock() < t0 + arrivals[k]:
+                time.sleep(0.0002)
+            jid = srv.submit(j["w"], hin, hout, j["T"], dtype=j["dtype"], bc="periodic", fusion_depth=j["fusion"],
+                             shape=j["shape"], arrival_s=t0 + arrivals[k])
+            inflight[jid] = (bi, i)
+        for jid, (bi, i) in list(inflight.items()):
+            srv.wait(jid)
+            if i in keep:
+                results[i] = pool_out[bi][:int(np.prod(jobs[i]["dims"]))].clone()
+        return results
+
+    # capacity: the first 48 jobs submitted at once
+    srv = binding.Server(budget, slots)
+    cal = list(range(48))
+    t_a = time.perf_counter()
+    run_trace(srv, cal, [0.0] * len(cal))
+    cal_s = time.perf_counter() - t_a
+    work_cal = sum(jobs[i]["T"] * int(np.prod(jobs[i]["dims"])) for i in cal)
+    srv.close()
+    cap = work_cal / cal_s  # point-steps per second
+    mean_work = np.mean([j["T"] * int(np.prod(j["dims"])) for j in jobs])
+    lam = 0.8 * cap / mean_work
+    rng = np.random.default_rng(5)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, n_jobs))
+    srv = binding.Server(budget, slots)
+    results = run_trace(srv, list(range(n_jobs)), list(arrivals))
+    st = srv.stats()
+    srv.close()
+    # alone vs mix on a sample of 2D and 3D jobs
+    same = True
+    checked = 0
+    for i in sorted(keep):
+        j = jobs[i]
+        x = torch.from_numpy(np.ascontiguousarray(grid_of(j))).cuda()
+        y = torch.empty_like(x)
+        if len(j["dims"]) == 3:
+            binding.direct_run(j["w"], x, y, torch.empty_like(x), j["T"], bc="periodic")
+        else:
+            p = binding.Plan(j["w"], j["dims"], dtype=j["dtype"], bc="periodic", fusion_depth=j["fusion"],
+                             shape=j["shape"])
+            p.run(x, y, j["T"])
+        same &= bool(torch.equal(y.cpu().reshape(-1), results[i].reshape(-1)))
+        checked += 1
+    print(json.dumps({"workload": f"C5: {n_jobs} Poisson-arrival jobs, 2D 5/9/13/49-pt 128-4096^2, "
+                                  "3D 7/27-pt 64-256^3, 10-500 steps, periodic",
+                      "budget_bytes": budget, "slots": slots, "arrival_rate_per_s": lam,
+                      "capacity_gstencil_s": cap / 1e9, "completed": st.completed, "failed": st.failed,
+                      "p50_ms": st.p50_s * 1e3, "p99_ms": st.p99_s * 1e3, "mean_ms": st.mean_s * 1e3,
+                      "max_ms": st.max_s * 1e3, "throughput_gstencil_s": st.gstencil_per_s,
+                      "peak_device_bytes": st.peak_bytes, "alone_equals_mix": same, "alone_checked": checked}),
+          flush=True)
 
 
 if __name__ == "__main__":

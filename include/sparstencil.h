@@ -221,6 +221,73 @@ sparstencil_status sparstencil_trace(int enable);
  * entries 960..1215: the same warps' stamps just before the chunk's proxy fence. */
 sparstencil_status sparstencil_trace_read(uint64_t* out, int n);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving: a request loop over the library (not in the paper; the runtime that takes
+ * stencil jobs as they arrive).  A dispatcher thread admits jobs in arrival order when one
+ * of `slots` execution slots (CUDA streams) is free and the job's device bytes fit under
+ * `hbm_budget_bytes` next to the jobs running; each admitted job copies its grid in, runs and
+ * copies its result out on its own stream, side by side with the others, and releases its
+ * slot and bytes when its last copy completes.  A job that can never fit the budget fails
+ * with SPST_ERR_NOMEM.  Plans are pooled by stencil and grid and reused by later jobs.
+ * 2D jobs run the sparse tensor-core path (sparstencil_run); 3D jobs run the FP32
+ * CUDA-core kernel (sparstencil_direct_run).  Results equal those of the same job run alone.
+ * --------------------------------------------------------------------------------------- */
+typedef struct sparstencil_server_s* sparstencil_server_t;
+
+typedef struct {
+  sparstencil_shape shape;
+  int radius;
+  const float* weights;      /* host cube as for sparstencil_plan, copied at submission */
+  int ndim;                  /* 2 or 3 */
+  const int64_t* dims;       /* copied at submission */
+  sparstencil_dtype dtype;   /* 2D jobs */
+  sparstencil_boundary bc;
+  int fusion_depth;          /* 2D jobs, as for sparstencil_plan */
+  int64_t timesteps;
+  const float* in_host;      /* host grid, read when the job is admitted (keep it valid until
+                                the job completes); page-locked memory lets the copies of
+                                different jobs overlap */
+  float* out_host;           /* host result, written before the job is reported complete */
+  double arrival_s;          /* arrival time on the server clock (sparstencil_server_clock);
+                                negative: the time of submission */
+} sparstencil_job;
+
+typedef struct {
+  int64_t job_id;
+  int status;                /* sparstencil_status of the job */
+  double arrival_s, admit_s, done_s;  /* server clock, seconds */
+  size_t device_bytes;       /* bytes counted against the budget while it ran */
+} sparstencil_job_result;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  double p50_s, p99_s, mean_s, max_s;  /* latency (completion - arrival) of completed jobs */
+  size_t peak_bytes;                   /* largest sum of admitted jobs' bytes */
+  double gstencil_per_s;               /* completed point-steps / (last completion - first arrival) */
+} sparstencil_server_summary;
+
+/* Starts a server on the current device.  slots in 1..64. */
+sparstencil_status sparstencil_server_create(size_t hbm_budget_bytes, int slots, sparstencil_server_t* out);
+/* Seconds since the server started (the clock of arrival_s and the results). */
+double sparstencil_server_clock(sparstencil_server_t server);
+/* Queues a job (plans it on the host now); *job_id receives its id.  Thread-safe. */
+sparstencil_status sparstencil_server_submit(sparstencil_server_t server, const sparstencil_job* job,
+                                             int64_t* job_id);
+/* Waits up to timeout_s for a job to finish; SPST_ERR_TIMEOUT if it has not. */
+sparstencil_status sparstencil_server_wait(sparstencil_server_t server, int64_t job_id, double timeout_s,
+                                           sparstencil_job_result* res);
+/* Waits up to timeout_s until no job is queued or running. */
+sparstencil_status sparstencil_server_drain(sparstencil_server_t server, double timeout_s);
+sparstencil_status sparstencil_server_stats(sparstencil_server_t server, sparstencil_server_summary* out);
+/* Finishes the queued and running jobs, then stops the server and frees its plans. */
+sparstencil_status sparstencil_server_destroy(sparstencil_server_t server);
+/* The admission policy replayed on the host (no device work): for n jobs with arrival
+ * times, run durations and device bytes, admit_s[i] / done_s[i] receive when job i would be
+ * admitted and finish (done = admit + duration), -1 for a job larger than the budget. */
+sparstencil_status sparstencil_server_simulate(size_t hbm_budget_bytes, int slots, int n, const double* arrival_s,
+                                               const double* duration_s, const size_t* bytes, double* admit_s,
+                                               double* done_s);
+
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char* sparstencil_last_error(void);
 

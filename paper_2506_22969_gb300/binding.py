@@ -40,13 +40,33 @@ class PlanInfo(ctypes.Structure):
                 ("bank_conflicts", ctypes.c_int)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int), ("radius", ctypes.c_int), ("weights", ctypes.c_void_p),
+                ("ndim", ctypes.c_int), ("dims", ctypes.c_void_p), ("dtype", ctypes.c_int), ("bc", ctypes.c_int),
+                ("fusion_depth", ctypes.c_int), ("timesteps", ctypes.c_int64), ("in_host", ctypes.c_void_p),
+                ("out_host", ctypes.c_void_p), ("arrival_s", ctypes.c_double)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("job_id", ctypes.c_int64), ("status", ctypes.c_int), ("arrival_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+class ServerSummary(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("mean_s", ctypes.c_double),
+                ("max_s", ctypes.c_double), ("peak_bytes", ctypes.c_size_t), ("gstencil_per_s", ctypes.c_double)]
+
+
 EXPORTS = ["sparstencil_plan", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host",
            "sparstencil_run_noalloc", "sparstencil_plan_destroy",
            "sparstencil_workspace_bytes", "sparstencil_bind_workspace", "sparstencil_run_batch", "sparstencil_query",
            "sparstencil_plan_tables", "sparstencil_table_kpad", "sparstencil_direct_run", "sparstencil_error_norms",
            "sparstencil_device_status", "sparstencil_set_wait_limit_ns", "sparstencil_trace",
            "sparstencil_trace_read", "sparstencil_last_error",
-           "sparstencil_version"]
+           "sparstencil_version", "sparstencil_server_create", "sparstencil_server_clock",
+           "sparstencil_server_submit", "sparstencil_server_wait", "sparstencil_server_drain",
+           "sparstencil_server_stats", "sparstencil_server_destroy", "sparstencil_server_simulate"]
 
 _lib = None
 
@@ -82,9 +102,18 @@ def load():
     lib.sparstencil_trace_read.argtypes = [vp, i32]
     lib.sparstencil_last_error.restype = ctypes.c_char_p
     lib.sparstencil_version.restype = ctypes.c_char_p
+    lib.sparstencil_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+    lib.sparstencil_server_clock.argtypes = [vp]
+    lib.sparstencil_server_clock.restype = ctypes.c_double
+    lib.sparstencil_server_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(i64)]
+    lib.sparstencil_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(JobResult)]
+    lib.sparstencil_server_drain.argtypes = [vp, ctypes.c_double]
+    lib.sparstencil_server_stats.argtypes = [vp, ctypes.POINTER(ServerSummary)]
+    lib.sparstencil_server_destroy.argtypes = [vp]
+    lib.sparstencil_server_simulate.argtypes = [ctypes.c_size_t, i32, i32, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name.startswith("sparstencil_") and name not in ("sparstencil_workspace_bytes", "sparstencil_last_error",
-                                                            "sparstencil_version"):
+                                                            "sparstencil_version", "sparstencil_server_clock"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -262,3 +291,89 @@ def run_batch(plans, xs, outs, steps, stream=None):
     op = (ctypes.c_void_p * n)(*[_dev_ptr(o).value for o in outs])
     st = (ctypes.c_int64 * n)(*[int(s) for s in steps])
     _check(load().sparstencil_run_batch(hp, ip, op, st, n, _stream_ptr(stream)))
+
+
+class Server:
+    """Stencil-job server (sparstencil_server_*): jobs are admitted in arrival order under an
+    HBM budget onto `slots` CUDA streams and run side by side."""
+
+    def __init__(self, hbm_budget_bytes: int, slots: int = 8):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.sparstencil_server_create(int(hbm_budget_bytes), int(slots), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}  # job id -> host arrays the server reads or writes
+
+    def clock(self) -> float:
+        return load().sparstencil_server_clock(self.handle)
+
+    def submit(self, weights, in_host, out_host, steps, dtype="bf16", bc="periodic", fusion_depth=1,
+               shape="box", arrival_s=-1.0) -> int:
+        """in_host / out_host: contiguous float32 numpy arrays or CPU torch tensors (page-locked
+        memory lets jobs' copies overlap); the server keeps references until the job is waited."""
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        ndim = w.ndim
+        shp = tuple(in_host.shape)
+        if len(shp) != ndim or tuple(out_host.shape) != shp:
+            raise ValueError("grid rank or shape mismatch")
+        d = np.asarray(shp, dtype=np.int64)
+        job = Job(_code(_SHAPES, shape), (w.shape[0] - 1) // 2, w.ctypes.data, ndim, d.ctypes.data,
+                  _code(_DTYPES, dtype), _code(_BCS, bc), int(fusion_depth), int(steps),
+                  _host_ptr(in_host), _host_ptr(out_host), float(arrival_s))
+        jid = ctypes.c_int64()
+        _check(load().sparstencil_server_submit(self.handle, ctypes.byref(job), ctypes.byref(jid)))
+        self._keep[jid.value] = (in_host, out_host)
+        return jid.value
+
+    def wait(self, job_id: int, timeout_s: float = 600.0) -> JobResult:
+        r = JobResult()
+        _check(load().sparstencil_server_wait(self.handle, int(job_id), float(timeout_s), ctypes.byref(r)))
+        self._keep.pop(job_id, None)
+        return r
+
+    def drain(self, timeout_s: float = 600.0):
+        _check(load().sparstencil_server_drain(self.handle, float(timeout_s)))
+
+    def stats(self) -> ServerSummary:
+        s = ServerSummary()
+        _check(load().sparstencil_server_stats(self.handle, ctypes.byref(s)))
+        return s
+
+    def close(self):
+        if self.handle:
+            _check(load().sparstencil_server_destroy(self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(a):
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+                raise TypeError("host grids must be contiguous float32 CPU tensors")
+            return a.data_ptr()
+    except ImportError:
+        pass
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+        raise TypeError("host grids must be contiguous float32 arrays")
+    return a.ctypes.data
+
+
+def server_simulate(budget: int, slots: int, arrival_s, duration_s, nbytes):
+    """The server's admission policy replayed on the host: (admit_s, done_s) per job."""
+    a = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    d = np.ascontiguousarray(duration_s, dtype=np.float64)
+    b = np.ascontiguousarray(nbytes, dtype=np.uint64)
+    n = a.size
+    adm = np.zeros(n)
+    done = np.zeros(n)
+    _check(load().sparstencil_server_simulate(int(budget), int(slots), n, a.ctypes.data, d.ctypes.data, b.ctypes.data,
+                                              adm.ctypes.data, done.ctypes.data))
+    return adm, done

@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libsparstencil.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 CU_SOURCES = ["sweep2d.cu", "aux.cu", "noalloc.cu"]
-CPP_SOURCES = ["planner.cpp", "capi.cpp"]
+CPP_SOURCES = ["planner.cpp", "capi.cpp", "server.cpp"]
 HEADERS = ["kernels.h", "planner.h"]
 
 
