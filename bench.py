@@ -424,7 +424,8 @@ def main():
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": cfg["name"], "grid": [H, W], "steps_per_run": T, "boundary": cfg["bc"],
                        "stencil": "box 3x3 (9-point), seeded random positive weights summing to 1",
-                       "precision": "bf16_split (weights 3 BF16 pieces, data hi+lo)", "fusion_depth": t_best,
+                       "precision": f"bf16_split (weights {info.mma_terms - 1} BF16 pieces, data hi+lo)",
+                       "fusion_depth": t_best,
                        "crush": [info.r1, info.r2], "kpad": info.kpad, "mma_terms": info.mma_terms,
                        "l2_flush": "512 MiB write before every timed run", "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_val, "unit": "GStencil/s", "h2d_bytes_per_step": H * W * 4,
