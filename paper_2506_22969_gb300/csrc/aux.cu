@@ -17,11 +17,22 @@ __device__ double g_norm_acc[4];
 // Copy-in: unpadded H x W -> padded (H + 2G) x Wp.  Ghost cells hold the periodic images
 // (periodic) or zeros (Dirichlet); columns beyond W + 2G are zero.
 // ---------------------------------------------------------------------------------------
+// Largest |v| seen by the calling warp's threads, folded into *maxabs (non-negative floats
+// order like their bit patterns).
+__device__ __forceinline__ void fold_maxabs(unsigned* maxabs, float m) {
+  if (!maxabs) return;
+  const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(m)));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxabs, b);
+}
+
 __global__ void pad_copy2d_kernel(const float* __restrict__ in, float* __restrict__ out, int H, int W, int G,
-                                  int64_t Wp, int periodic) {
+                                  int64_t Wp, int periodic, unsigned* maxabs) {
   const int64_t Hp = (int64_t)H + 2 * G;
   const int64_t total = Hp * Wp;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+  float m = 0.f;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < total; i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + threadIdx.x;
+    if (i >= total) continue;
     const int64_t yp = i / Wp, xp = i % Wp;
     int64_t y = yp - G, x = xp - G;
     float v = 0.f;
@@ -35,7 +46,9 @@ __global__ void pad_copy2d_kernel(const float* __restrict__ in, float* __restric
       }
     }
     out[i] = v;
+    m = fmaxf(m, fabsf(v));
   }
+  fold_maxabs(maxabs, m);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -231,14 +244,86 @@ __global__ void band2d_kernel(const BandParams p) {
   }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// 3D copy-in: unpadded D x H x W -> padded (D + 2G) x (H + 2G) x Wp; ghost cells hold the
+// periodic images or zeros; columns beyond W + 2G are zero.  One thread per padded cell.
+// ---------------------------------------------------------------------------------------
+__global__ void pad_copy3d_kernel(const float* __restrict__ in, float* __restrict__ out, int D, int H, int W, int G,
+                                  int64_t Wp, int periodic, unsigned* maxabs) {
+  const int64_t Hp = (int64_t)H + 2 * G, Dp = (int64_t)D + 2 * G;
+  const int64_t total = Dp * Hp * Wp;
+  float m = 0.f;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < total; i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + threadIdx.x;
+    if (i >= total) continue;
+    const int64_t xp = i % Wp, yp = (i / Wp) % Hp, zp = i / (Wp * Hp);
+    int64_t z = zp - G, y = yp - G, x = xp - G;
+    float v = 0.f;
+    if (xp < (int64_t)W + 2 * G) {
+      if (periodic) {
+        z = z < 0 ? z + D : (z >= D ? z - D : z);
+        y = y < 0 ? y + H : (y >= H ? y - H : y);
+        x = x < 0 ? x + W : (x >= W ? x - W : x);
+        v = in[(z * H + y) * W + x];
+      } else if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W) {
+        v = in[(z * H + y) * W + x];
+      }
+    }
+    out[i] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+  fold_maxabs(maxabs, m);
+}
+
+// Periodic ghost shell of a padded 3D grid rewritten from the interior it wraps to (after a
+// sweep that wrote the interior only).  One thread per padded cell of each padded row; rows
+// wholly in the interior only touch their 2G ghost columns.
+__global__ void ghost_refresh3d_kernel(float* __restrict__ g3, int D, int H, int W, int G, int64_t Wp) {
+  const int64_t Hp = (int64_t)H + 2 * G, Dp = (int64_t)D + 2 * G;
+  const int64_t rows = Dp * Hp;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int64_t yp = r % Hp, zp = r / Hp;
+    const bool ghost_row = yp < G || yp >= H + G || zp < G || zp >= D + G;
+    int64_t z = zp - G, y = yp - G;
+    z = z < 0 ? z + D : (z >= D ? z - D : z);
+    y = y < 0 ? y + H : (y >= H ? y - H : y);
+    const float* src = g3 + ((z + G) * Hp + (y + G)) * Wp + G;
+    float* dst = g3 + r * Wp;
+    for (int64_t xp = threadIdx.x; xp < (int64_t)W + 2 * G; xp += blockDim.x) {
+      const bool ghost_col = xp < G || xp >= W + G;
+      if (!ghost_row && !ghost_col) continue;
+      int64_t x = xp - G;
+      x = x < 0 ? x + W : (x >= W ? x - W : x);
+      dst[xp] = src[x];
+    }
+  }
+}
+
 }  // namespace
 
+cudaError_t launch_pad_copy3d(const float* in, float* padded, int D, int H, int W, int G, int64_t Wp, int periodic,
+                              unsigned* maxabs, cudaStream_t stream) {
+  const int64_t total = ((int64_t)D + 2 * G) * ((int64_t)H + 2 * G) * Wp;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  pad_copy3d_kernel<<<(unsigned)blocks, 256, 0, stream>>>(in, padded, D, H, W, G, Wp, periodic, maxabs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ghost_refresh3d(float* padded, int D, int H, int W, int G, int64_t Wp, cudaStream_t stream) {
+  const int64_t rows = ((int64_t)D + 2 * G) * ((int64_t)H + 2 * G);
+  const int64_t blocks = rows < 152 * 32 ? rows : 152 * 32;
+  ghost_refresh3d_kernel<<<(unsigned)blocks, 128, 0, stream>>>(padded, D, H, W, G, Wp);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pad_copy2d(const float* in, float* padded, int H, int W, int G, int64_t Wp, int periodic,
-                              cudaStream_t stream) {
+                              unsigned* maxabs, cudaStream_t stream) {
   const int64_t total = ((int64_t)H + 2 * G) * Wp;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  pad_copy2d_kernel<<<(unsigned)blocks, 256, 0, stream>>>(in, padded, H, W, G, Wp, periodic);
+  pad_copy2d_kernel<<<(unsigned)blocks, 256, 0, stream>>>(in, padded, H, W, G, Wp, periodic, maxabs);
   return cudaGetLastError();
 }
 

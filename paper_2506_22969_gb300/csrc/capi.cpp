@@ -21,6 +21,7 @@
 using spst::PlanGeometry;
 using spst::SweepTables;
 using spst::Tile2D;
+using spst::Tile3D;
 
 namespace {
 
@@ -111,6 +112,8 @@ struct sparstencil_plan_s {
   CUtensorMap tmap[2];
   float* stage_in = nullptr;
   float* stage_out = nullptr;
+  unsigned* maxabs = nullptr;  // FP16 operands: max |input| of the current run (device word)
+  float growth = 1.f;          // bound on max|u| / max|u0| over the current run
 
   ~sparstencil_plan_s() {
     int cur = -1;
@@ -120,10 +123,12 @@ struct sparstencil_plan_s {
     if (ws_owned) cudaFree(ws);
     cudaFree(stage_in);
     cudaFree(stage_out);
+    cudaFree(maxabs);
     if (cur >= 0) cudaSetDevice(cur);
   }
 
-  size_t grid_floats() const { return (size_t)geo.Hp * (size_t)geo.Wp; }
+  size_t grid_floats() const { return (size_t)geo.Dp * (size_t)geo.Hp * (size_t)geo.Wp; }
+  size_t cells() const { return (size_t)geo.D * (size_t)geo.H * (size_t)geo.W; }
   float* pad(int i) const { return (float*)((char*)ws + (size_t)i * ((grid_floats() * 4 + 255) & ~(size_t)255)); }
 };
 
@@ -131,13 +136,16 @@ namespace {
 
 std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
   std::vector<double> wf = spst::compose_weights(p->w64, p->ndim, p->radius, depth);
-  // Weight pieces: single-word operands use two 16-bit pieces, split operands three (exact
-  // for FP32 weights).  A fused split sweep (t >= 2) whose three pieces would leave TMEM room
-  // for only one accumulator uses two: the second accumulator lets the next tile's MMAs overlap
-  // this tile's write-back and the fourth MMA term goes away, while the weight rounding
-  // (<= 2^-17 relative per fused weight) is shared by t steps; measured on the periodic Fourier
-  // closed form over 100 steps at t = 3 the rel-L2 error stays below 1e-6.
-  const int pieces = is_split(p->dtype) ? 3 : 2;
+  // Weight pieces: single-word operands use two 16-bit pieces.  BF16 split operands use three
+  // (exact for FP32 weights); FP16 split operands two, which hold 22 significant bits of each
+  // scaled weight: a third FP16 piece sits below the rounding of the FP32 accumulator it is
+  // added to and would only cost an MMA term.  A fused BF16 split sweep (t >= 2) whose three
+  // pieces would leave TMEM room for only one accumulator uses two: the second accumulator lets
+  // the next tile's MMAs overlap this tile's write-back and the fourth MMA term goes away,
+  // while the weight rounding (<= 2^-17 relative per fused weight) is shared by t steps;
+  // measured on the periodic Fourier closed form over 100 steps at t = 3 the rel-L2 error stays
+  // below 1e-6.
+  const int pieces = (is_split(p->dtype) && word_of(p->dtype) == spst::Word::BF16) ? 3 : 2;
   std::string err = spst::build_sweep_tables_2d(wf, depth * p->radius, p->geo, word_of(p->dtype), pieces, true, out);
   if (!err.empty()) return err;
   if (pieces == 3 && depth >= 2 && tmem_accumulators(*out) < 2) {
@@ -155,17 +163,23 @@ std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
 // returns an empty string or the reason the grid cannot be planned.
 std::string plan_geometry(sparstencil_plan_t p) {
   PlanGeometry& g = p->geo;
+  const bool d3 = g.ndim == 3;
   g.G = p->t_max * p->radius;
   if (g.G > 60) return "fused radius too large";
-  if (g.H < 2 * g.G || g.W < 2 * g.G || g.W < 4) return "grid smaller than twice the fused radius";
-  if (g.H > (1 << 30) || g.W > (1 << 30)) return "grid extent too large";
+  if (g.H < 2 * g.G || g.W < 2 * g.G || g.W < 4 || (d3 && g.D < 2 * g.G))
+    return "grid smaller than twice the fused radius";
+  if (g.H > (1 << 30) || g.W > (1 << 30) || g.D > (1 << 30)) return "grid extent too large";
   g.Hp = g.H + 2 * g.G;
+  g.Dp = d3 ? g.D + 2 * g.G : 1;
   g.Wp = ((g.W + 2 * g.G) + 3) / 4 * 4;
-  g.P = (Tile2D::TX + 2 * g.G + 3) / 4 * 4;
-  g.box_h = Tile2D::TY + 2 * g.G;
-  g.tiles_x = (g.W + Tile2D::TX - 1) / Tile2D::TX;
-  g.tiles_y = (g.H + Tile2D::TY - 1) / Tile2D::TY;
-  g.num_tiles = g.tiles_x * g.tiles_y;
+  const int tx = d3 ? Tile3D::TX : Tile2D::TX, ty = d3 ? Tile3D::TY : Tile2D::TY;
+  g.P = (tx + 2 * g.G + 3) / 4 * 4;
+  g.box_h = ty + 2 * g.G;
+  g.box_d = d3 ? Tile3D::TZ + 2 * g.G : 1;
+  g.tiles_x = (g.W + tx - 1) / tx;
+  g.tiles_y = (g.H + ty - 1) / ty;
+  g.tiles_z = d3 ? (g.D + Tile3D::TZ - 1) / Tile3D::TZ : 1;
+  g.num_tiles = g.tiles_x * g.tiles_y * g.tiles_z;
   if (g.num_tiles > (1ll << 30)) return "too many tiles";
   return "";
 }
@@ -220,14 +234,26 @@ cudaError_t launch_band(sparstencil_plan_t p, int depth, const float* src, float
 sparstencil_status make_tmaps(sparstencil_plan_t p) {
   EncodeTiledFn enc = get_encode_tiled();
   if (!enc) return fail(SPST_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  const PlanGeometry& g = p->geo;
   for (int i = 0; i < 2; i++) {
-    cuuint64_t gdim[2] = {(cuuint64_t)p->geo.Wp, (cuuint64_t)p->geo.Hp};
-    cuuint64_t gstr[1] = {(cuuint64_t)p->geo.Wp * 4};
-    cuuint32_t box[2] = {(cuuint32_t)p->geo.P, (cuuint32_t)p->geo.box_h};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(&p->tmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->pad(i), gdim, gstr, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r;
+    if (g.ndim == 3) {
+      cuuint64_t gdim[3] = {(cuuint64_t)g.Wp, (cuuint64_t)g.Hp, (cuuint64_t)g.Dp};
+      cuuint64_t gstr[2] = {(cuuint64_t)g.Wp * 4, (cuuint64_t)g.Wp * (cuuint64_t)g.Hp * 4};
+      cuuint32_t box[3] = {(cuuint32_t)g.P, (cuuint32_t)g.box_h, (cuuint32_t)g.box_d};
+      cuuint32_t es[3] = {1, 1, 1};
+      r = enc(&p->tmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->pad(i), gdim, gstr, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+      cuuint64_t gdim[2] = {(cuuint64_t)g.Wp, (cuuint64_t)g.Hp};
+      cuuint64_t gstr[1] = {(cuuint64_t)g.Wp * 4};
+      cuuint32_t box[2] = {(cuuint32_t)g.P, (cuuint32_t)g.box_h};
+      cuuint32_t es[2] = {1, 1};
+      r = enc(&p->tmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->pad(i), gdim, gstr, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS) return fail(SPST_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   }
   return SPST_OK;
@@ -257,6 +283,14 @@ sparstencil_status ensure_device(sparstencil_plan_t p, cudaStream_t stream) {
     p->ws_owned = true;
     SPST_CUDA(cudaMemsetAsync(w, 0, need, stream), "zero workspace");
     p->ws_ready = false;
+  }
+  if (!p->maxabs && word_of(p->dtype) == spst::Word::FP16) {
+    void* m = nullptr;
+    if (cudaMalloc(&m, sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SPST_ERR_NOMEM, "allocation of the data-scale word failed");
+    }
+    p->maxabs = (unsigned*)m;
   }
   if (!p->ws_ready) {
     sparstencil_status s = make_tmaps(p);
@@ -289,12 +323,16 @@ spst::Sweep2DParams sweep_params(sparstencil_plan_t p, const SweepTables& T, con
   std::memset(&prm, 0, sizeof(prm));
   prm.H = (int)g.H;
   prm.W = (int)g.W;
+  prm.D = (int)g.D;
+  prm.dim3 = g.ndim == 3 ? 1 : 0;
   prm.G = g.G;
   prm.tiles_x = (int)g.tiles_x;
   prm.tiles_y = (int)g.tiles_y;
+  prm.tiles_z = (int)g.tiles_z;
   prm.num_tiles = (int)g.num_tiles;
   prm.P = g.P;
   prm.box_h = g.box_h;
+  prm.box_d = g.box_d;
   prm.kpad = T.kpad;
   prm.kchunks = T.kpad / 32;
   prm.a_pieces = T.a_pieces;
@@ -318,6 +356,8 @@ spst::Sweep2DParams sweep_params(sparstencil_plan_t p, const SweepTables& T, con
   prm.meta_words = dt.meta;
   prm.S_hi = T.S_hi;
   prm.S_lo = T.S_lo;
+  prm.maxabs = p->maxabs;
+  prm.growth = p->growth;
   prm.status = status;
   prm.wait_ns = g_wait_ns;
   return prm;
@@ -327,13 +367,54 @@ spst::Sweep2DParams sweep_params(sparstencil_plan_t p, const SweepTables& T, con
 // done by measurement): copies `in` into the padded grid, times two sweeps of every
 // candidate depth after one warm-up sweep, and keeps the depth with the least time per time
 // step.  Synchronises the stream; the caller's run then starts from a fresh copy-in.
-sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStream_t stream) {
+// Copy-in of a caller grid into the plan's padded grid `pad` (2D or 3D).
+// FP16 plans also record max |in| for the data scale (see Sweep2DParams::maxabs), and
+// `steps` (the run's time steps) bounds its growth: max|u| <= max|u0| * (sum |w|)^steps.
+cudaError_t copy_in(sparstencil_plan_t p, const float* in, float* pad, int64_t steps, cudaStream_t stream,
+                    unsigned* maxabs) {
   const PlanGeometry& g = p->geo;
+  const int periodic = p->bc == SPST_PERIODIC ? 1 : 0;
+  if (maxabs) {
+    cudaError_t e = cudaMemsetAsync(maxabs, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    double sabs = 0.0;
+    for (double w : p->w64) sabs += std::fabs(w);
+    const double growth = std::pow(std::max(sabs, 1.0), (double)steps);
+    p->growth = (float)std::min(growth, 1e30);
+  }
+  if (g.ndim == 3)
+    return spst::launch_pad_copy3d(in, pad, (int)g.D, (int)g.H, (int)g.W, g.G, g.Wp, periodic, maxabs, stream);
+  return spst::launch_pad_copy2d(in, pad, (int)g.H, (int)g.W, g.G, g.Wp, periodic, maxabs, stream);
+}
+
+// Output parameters of a sweep that writes the padded grid `pad` (or, last, the caller's
+// unpadded `out`).  A 3D sweep writes the interior only; its periodic ghost shell is then
+// refreshed by after_sweep.
+void set_output(sparstencil_plan_t p, spst::Sweep2DParams* prm, float* pad, float* out, bool last) {
+  const PlanGeometry& g = p->geo;
+  prm->out = last ? out : pad;
+  prm->out_pitch = last ? g.W : g.Wp;
+  prm->out_plane = last ? g.W * g.H : g.Wp * g.Hp;
+  prm->out_off = last ? 0 : g.G;
+  prm->out_ghost = (!last && p->bc == SPST_PERIODIC && g.ndim == 2) ? 1 : 0;
+}
+
+// Work after a sweep of depth `depth` from padded grid `src` into prm.out: the Dirichlet band
+// of a fused 2D sweep, or the periodic ghost shell of a 3D padded output.
+cudaError_t after_sweep(sparstencil_plan_t p, int depth, const float* src, const spst::Sweep2DParams& prm, bool last,
+                        cudaStream_t stream) {
+  const PlanGeometry& g = p->geo;
+  if (g.ndim == 3) {
+    if (last || p->bc != SPST_PERIODIC) return cudaSuccess;
+    return spst::launch_ghost_refresh3d(prm.out, (int)g.D, (int)g.H, (int)g.W, g.G, g.Wp, stream);
+  }
+  return launch_band(p, depth, src, prm.out, prm.out_pitch, prm.out_off, stream);
+}
+
+sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStream_t stream) {
   int* status = spst::device_status_word();
   if (!status) return fail(SPST_ERR_CUDA, "device status word unavailable");
-  SPST_CUDA(spst::launch_pad_copy2d(in, p->pad(0), (int)g.H, (int)g.W, g.G, g.Wp, p->bc == SPST_PERIODIC ? 1 : 0,
-                                    stream),
-            "pad copy");
+  SPST_CUDA(copy_in(p, in, p->pad(0), 3 * p->t_max, stream, p->maxabs), "pad copy");
   cudaEvent_t e0, e1;
   SPST_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -354,12 +435,9 @@ sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStr
     for (int k = 0; k < 3 && s == SPST_OK; k++) {
       if (k == 1 && cudaEventRecord(e0, stream) != cudaSuccess) s = fail(SPST_ERR_CUDA, "cudaEventRecord");
       spst::Sweep2DParams prm = sweep_params(p, *T, *dt, status);
-      prm.out = p->pad(1 - cur);
-      prm.out_pitch = g.Wp;
-      prm.out_off = g.G;
-      prm.out_ghost = p->bc == SPST_PERIODIC ? 1 : 0;
+      set_output(p, &prm, p->pad(1 - cur), nullptr, false);
       if (spst::launch_sweep2d(p->tmap[cur], prm, p->num_sms, stream) != cudaSuccess ||
-          launch_band(p, depth, p->pad(cur), prm.out, prm.out_pitch, prm.out_off, stream) != cudaSuccess)
+          after_sweep(p, depth, p->pad(cur), prm, false, stream) != cudaSuccess)
         s = fail(SPST_ERR_CUDA, "autotune sweep launch");
       cur = 1 - cur;
     }
@@ -397,9 +475,8 @@ sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out,
                               LaunchTimer* timer = nullptr) {
   sparstencil_status s = ensure_device(p, stream);
   if (s != SPST_OK) return s;
-  const PlanGeometry& g = p->geo;
   if (T == 0) {
-    SPST_CUDA(cudaMemcpyAsync(out, in, (size_t)g.H * g.W * 4, cudaMemcpyDeviceToDevice, stream), "copy in->out");
+    SPST_CUDA(cudaMemcpyAsync(out, in, p->cells() * 4, cudaMemcpyDeviceToDevice, stream), "copy in->out");
     return SPST_OK;
   }
   if (p->autotune_pending && (s = autotune_depth(p, in, stream)) != SPST_OK) return s;
@@ -420,20 +497,15 @@ sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out,
     if (s != SPST_OK) return s;
   }
   if (timer && (s = timer->record(stream)) != SPST_OK) return s;
-  SPST_CUDA(spst::launch_pad_copy2d(in, p->pad(0), (int)g.H, (int)g.W, g.G, g.Wp, p->bc == SPST_PERIODIC ? 1 : 0,
-                                    stream),
-            "pad copy");
+  SPST_CUDA(copy_in(p, in, p->pad(0), T, stream, p->maxabs), "pad copy");
   if (timer && (s = timer->record(stream)) != SPST_OK) return s;
   int cur = 0;
   for (size_t i = 0; i < sweeps.size(); i++) {
     const bool last = (i + 1 == sweeps.size());
     spst::Sweep2DParams prm = sweep_params(p, *tabs[i], *dtabs[i], status);
-    prm.out = last ? out : p->pad(1 - cur);
-    prm.out_pitch = last ? g.W : g.Wp;
-    prm.out_off = last ? 0 : g.G;
-    prm.out_ghost = (!last && p->bc == SPST_PERIODIC) ? 1 : 0;
+    set_output(p, &prm, p->pad(1 - cur), out, last);
     SPST_CUDA(spst::launch_sweep2d(p->tmap[cur], prm, p->num_sms, stream), "sweep launch");
-    SPST_CUDA(launch_band(p, sweeps[i], p->pad(cur), prm.out, prm.out_pitch, prm.out_off, stream), "band launch");
+    SPST_CUDA(after_sweep(p, sweeps[i], p->pad(cur), prm, last, stream), "band or ghost launch");
     cur = 1 - cur;
   }
   // one event after all sweeps: an event between two sweeps would stop the next one from
@@ -475,7 +547,7 @@ sparstencil_status report_error(sparstencil_status s, const char* msg) { return 
 
 sparstencil_status run_plan_with_buffers(sparstencil_plan_t p, const float* in, float* out, int64_t T,
                                          cudaStream_t stream, float* scratch, size_t scratch_floats,
-                                         uint32_t* tables, size_t table_words) {
+                                         uint32_t* tables, size_t table_words, unsigned* maxabs_word) {
   if (!p || !in || !out) return fail(SPST_ERR_INVALID, "null plan or grid");
   if (T < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
   if (in == out) return fail(SPST_ERR_INVALID, "in and out must not alias");
@@ -486,13 +558,14 @@ sparstencil_status run_plan_with_buffers(sparstencil_plan_t p, const float* in, 
   SPST_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
   if (major != 10 || minor != 3) return fail(SPST_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300)");
   const PlanGeometry& g = p->geo;
+  if (g.ndim != 2) return fail(SPST_ERR_UNSUPPORTED, "the allocation-free path runs 2D plans only");
   const size_t grid = ((size_t)g.Hp * (size_t)g.Wp + 63) & ~(size_t)63;  // 256-byte aligned grids
   if (2 * grid > scratch_floats)
     return fail(SPST_ERR_UNSUPPORTED, "grid too large for the allocation-free path: needs " + std::to_string(grid) +
                                           " padded cells per ping-pong grid, the static scratch holds " +
                                           std::to_string(scratch_floats / 2));
   if (T == 0) {
-    SPST_CUDA(cudaMemcpyAsync(out, in, (size_t)g.H * g.W * 4, cudaMemcpyDeviceToDevice, stream), "copy in->out");
+    SPST_CUDA(cudaMemcpyAsync(out, in, p->cells() * 4, cudaMemcpyDeviceToDevice, stream), "copy in->out");
     return SPST_OK;
   }
   std::vector<int> sweeps((size_t)(T / p->t), p->t);
@@ -549,8 +622,8 @@ sparstencil_status run_plan_with_buffers(sparstencil_plan_t p, const float* in, 
   // the static arrays keep the previous call's contents: the second grid's ghost cells and
   // slack columns must start at zero (the copy-in writes every cell of the first grid)
   SPST_CUDA(cudaMemsetAsync(pad[1], 0, grid * 4, stream), "clear scratch");
-  SPST_CUDA(launch_pad_copy2d(in, pad[0], (int)g.H, (int)g.W, g.G, g.Wp, p->bc == SPST_PERIODIC ? 1 : 0, stream),
-            "pad copy");
+  unsigned* maxabs = word_of(p->dtype) == Word::FP16 ? maxabs_word : nullptr;
+  SPST_CUDA(copy_in(p, in, pad[0], T, stream, maxabs), "pad copy");
   int cur = 0;
   for (size_t i = 0; i < sweeps.size(); i++) {
     const Region* rg = nullptr;
@@ -562,10 +635,8 @@ sparstencil_status run_plan_with_buffers(sparstencil_plan_t p, const float* in, 
     dtv.a_words = rg->a_words;
     dtv.meta = rg->meta;
     Sweep2DParams prm = sweep_params(p, *rg->T, dtv, status);  // dtv borrows the static tables
-    prm.out = last ? out : pad[1 - cur];
-    prm.out_pitch = last ? g.W : g.Wp;
-    prm.out_off = last ? 0 : g.G;
-    prm.out_ghost = (!last && p->bc == SPST_PERIODIC) ? 1 : 0;
+    prm.maxabs = maxabs;
+    set_output(p, &prm, pad[1 - cur], out, last);
     prm.status = status;
     prm.wait_ns = g_wait_ns;
     SPST_CUDA(launch_sweep2d(tm[cur], prm, sms, stream), "sweep launch");
@@ -600,7 +671,7 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   if (bc != SPST_DIRICHLET_ZERO && bc != SPST_PERIODIC) return fail(SPST_ERR_INVALID, "bad boundary");
   if (radius < 1) return fail(SPST_ERR_INVALID, "radius must be >= 1");
   if (fusion_depth < 0) return fail(SPST_ERR_INVALID, "fusion_depth must be >= 0");
-  if (ndim != 2) return fail(SPST_ERR_UNSUPPORTED, "only 2D grids are supported by this build");
+  if (ndim != 2 && ndim != 3) return fail(SPST_ERR_UNSUPPORTED, "ndim must be 2 or 3");
   for (int i = 0; i < ndim; i++)
     if (dims[i] <= 0) return fail(SPST_ERR_INVALID, "grid extents must be positive");
   if (!shape_mask_ok(shape, ndim, radius, weights))
@@ -614,19 +685,20 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   p->bc = bc;
   p->requested_t = fusion_depth;
   p->t = fusion_depth == 0 ? 1 : fusion_depth;
-  if (bc == SPST_DIRICHLET_ZERO && p->t > 1 && radius > 4)
-    return fail(SPST_ERR_UNSUPPORTED, "temporal fusion with a Dirichlet boundary needs radius <= 4");
+  if (bc == SPST_DIRICHLET_ZERO && p->t > 1 && (radius > 4 || ndim == 3))
+    return fail(SPST_ERR_UNSUPPORTED, "temporal fusion with a Dirichlet boundary needs a 2D grid and radius <= 4");
   p->t_max = p->t;
   // fusion_depth 0: the deepest of 3, 2, 1 whose tables fit is planned; the first run times
   // every depth up to it and keeps the fastest per time step
-  const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && radius > 4) ? 1 : 3) : p->t;
+  const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && (radius > 4 || ndim == 3)) ? 1 : 3) : p->t;
   const int side = 2 * radius + 1;
-  p->w64.resize((size_t)side * side);
+  p->w64.resize((size_t)side * side * (ndim == 3 ? side : 1));
   for (size_t i = 0; i < p->w64.size(); i++) p->w64[i] = (double)weights[i];
   PlanGeometry& g = p->geo;
-  g.ndim = 2;
-  g.H = dims[0];
-  g.W = dims[1];
+  g.ndim = ndim;
+  g.D = ndim == 3 ? dims[0] : 1;
+  g.H = dims[ndim - 2];
+  g.W = dims[ndim - 1];
   std::string err;
   for (int tm = t_try; tm >= 1; tm--) {
     p->t = p->t_max = tm;
@@ -637,6 +709,7 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
       std::memset(&probe, 0, sizeof(probe));
       probe.P = g.P;
       probe.box_h = g.box_h;
+      probe.box_d = g.box_d;
       probe.kpad = p->full.kpad;
       probe.kchunks = p->full.kpad / 32;
       probe.a_pieces = p->full.a_pieces;
@@ -716,7 +789,7 @@ sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in
   if (timesteps < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
   sparstencil_status s = ensure_device(plan, stream);
   if (s != SPST_OK) return s;
-  const size_t bytes = (size_t)plan->geo.H * plan->geo.W * 4;
+  const size_t bytes = plan->cells() * 4;
   if (!plan->stage_in) {
     if (cudaMalloc(&plan->stage_in, bytes) != cudaSuccess || cudaMalloc(&plan->stage_out, bytes) != cudaSuccess) {
       cudaGetLastError();

@@ -22,9 +22,11 @@ constexpr int kSBO = 576;              // bytes between 8-patch groups
 
 struct Sweep2DParams {
   int H, W;             // true grid extents (rows, columns)
+  int D;                // planes (3D; 1 for 2D)
+  int dim3;             // 1: 3D sweep (Tile3D patches and tiles, 3D TMA box)
   int G;                // ghost width of the input padded grid
-  int tiles_x, tiles_y, num_tiles;
-  int P, box_h;         // shared-memory tile pitch (floats) and height (rows) = TMA box
+  int tiles_x, tiles_y, tiles_z, num_tiles;
+  int P, box_h, box_d;  // shared-memory tile pitch (floats), height (rows), depth (planes) = TMA box
   int kpad, kchunks;    // K after padding, number of 32-wide chunks
   int a_pieces;         // 16-bit pieces of the weights resident in TMEM (1..3)
   int b_pieces;         // 16-bit pieces of the grid data per B'' element (1: single word, 2: hi + lo)
@@ -41,8 +43,15 @@ struct Sweep2DParams {
   float S_hi, S_lo;     // sum of the sweep's weights as an FP32 pair
   float* out;           // output grid base
   int64_t out_pitch;    // floats per output row
+  int64_t out_plane;    // floats per output plane (3D)
   int out_off;          // ghost width of the output grid (0 for an unpadded grid)
   int out_ghost;        // 1: periodic padded output, also write the ghost images
+  // FP16 operands: the grid data enter B'' scaled by 2^k, k = floor(log2(2^13 / (2 max|u0|
+  // growth))), so that hi and lo pieces stay normal; max|u0| is read from *maxabs (written by
+  // the copy-in), growth bounds max|u| / max|u0| over the run (sum of |w| to the power of
+  // the steps).  maxabs null: k = 0.
+  const unsigned* maxabs;
+  float growth;
   int* status;          // device status word
   unsigned long long wait_ns;  // bound of every device-side wait
 };
@@ -67,8 +76,14 @@ cudaError_t sweep_trace_read(unsigned long long* out, int n);
 
 // Copies an unpadded H x W grid into a padded (H+2G) x Wp grid: interior, ghosts (periodic
 // images or zeros) and the slack columns (zeros).
+// maxabs (may be null): receives max |in| (atomicMax on the float bits; the caller zeroes it).
 cudaError_t launch_pad_copy2d(const float* in, float* padded, int H, int W, int G, int64_t Wp, int periodic,
-                              cudaStream_t stream);
+                              unsigned* maxabs, cudaStream_t stream);
+// 3D copy-in: unpadded D x H x W -> padded (D + 2G) x (H + 2G) x Wp.
+cudaError_t launch_pad_copy3d(const float* in, float* padded, int D, int H, int W, int G, int64_t Wp, int periodic,
+                              unsigned* maxabs, cudaStream_t stream);
+// Rewrites the periodic ghost shell of a padded 3D grid from its interior.
+cudaError_t launch_ghost_refresh3d(float* padded, int D, int H, int W, int G, int64_t Wp, cudaStream_t stream);
 
 struct DirectParams {
   int ndim;

@@ -20,7 +20,7 @@ sparstencil_status report_error(sparstencil_status s, const char* msg);
 // Runs a plan with caller-provided device buffers (implemented in capi.cpp).
 sparstencil_status run_plan_with_buffers(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
                                          cudaStream_t stream, float* scratch, size_t scratch_floats,
-                                         uint32_t* tables, size_t table_words);
+                                         uint32_t* tables, size_t table_words, unsigned* maxabs_word);
 }  // namespace spst
 
 namespace {
@@ -33,11 +33,14 @@ constexpr size_t kNoAllocTableWords = (size_t)128 << 10;
 
 static __device__ __align__(256) float g_noalloc_scratch[2 * kNoAllocGridFloats];
 static __device__ __align__(256) uint32_t g_noalloc_tables[kNoAllocTableWords];
+// max |input| of the current run (FP16 operands' data scale)
+static __device__ unsigned g_noalloc_maxabs;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 float* g_scratch_ptr[kMaxDevices] = {nullptr};
 uint32_t* g_tables_ptr[kMaxDevices] = {nullptr};
+unsigned* g_maxabs_ptr[kMaxDevices] = {nullptr};
 
 }  // namespace
 
@@ -48,6 +51,7 @@ extern "C" sparstencil_status sparstencil_run_noalloc(sparstencil_plan_t plan, c
   if (dev < 0 || dev >= kMaxDevices) return spst::report_error(SPST_ERR_UNSUPPORTED, "device index out of range");
   float* scratch = nullptr;
   uint32_t* tables = nullptr;
+  unsigned* maxabs = nullptr;
   {
     // One-time set-up per device, with that device current: the host-side names of the
     // arrays are not device addresses, so resolve them with cudaGetSymbolAddress.
@@ -59,12 +63,17 @@ extern "C" sparstencil_status sparstencil_run_noalloc(sparstencil_plan_t plan, c
         return spst::report_error(SPST_ERR_CUDA, "cudaGetSymbolAddress(static scratch) failed");
       if (cudaGetSymbolAddress(&t, g_noalloc_tables) != cudaSuccess)
         return spst::report_error(SPST_ERR_CUDA, "cudaGetSymbolAddress(static tables) failed");
+      void* m = nullptr;
+      if (cudaGetSymbolAddress(&m, g_noalloc_maxabs) != cudaSuccess)
+        return spst::report_error(SPST_ERR_CUDA, "cudaGetSymbolAddress(static data-scale word) failed");
       g_scratch_ptr[dev] = (float*)s;
       g_tables_ptr[dev] = (uint32_t*)t;
+      g_maxabs_ptr[dev] = (unsigned*)m;
     }
     scratch = g_scratch_ptr[dev];
     tables = g_tables_ptr[dev];
+    maxabs = g_maxabs_ptr[dev];
   }
   return spst::run_plan_with_buffers(plan, in, out, timesteps, stream, scratch, 2 * kNoAllocGridFloats, tables,
-                                     kNoAllocTableWords);
+                                     kNoAllocTableWords, maxabs);
 }

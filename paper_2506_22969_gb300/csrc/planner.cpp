@@ -143,6 +143,32 @@ std::vector<std::pair<int, int>> hierarchical_matching(int n, int g, int k) {
   return out;
 }
 
+std::vector<std::pair<int, int>> hierarchical_matching_nd(const std::vector<int>& sizes, int k) {
+  if (sizes.size() == 2) return hierarchical_matching(sizes[0] * sizes[1], sizes[1], k);
+  std::vector<std::pair<int, int>> out;
+  if (sizes.size() < 2) return out;
+  const int m = sizes[0];
+  int inner = 1;
+  for (size_t i = 1; i < sizes.size(); i++) inner *= sizes[i];
+  const int s0 = std::max(m / 2, k);
+  std::vector<char> matched(m, 0);
+  std::vector<std::pair<int, int>> top;
+  for (int i = 0; i < m; i++)
+    if (!matched[i] && i + s0 < m && !matched[i + s0]) {
+      top.push_back({i, i + s0});
+      matched[i] = matched[i + s0] = 1;
+    }
+  for (auto& bp : top)
+    for (int t = 0; t < inner; t++) out.push_back({bp.first * inner + t, bp.second * inner + t});
+  const std::vector<int> rest(sizes.begin() + 1, sizes.end());
+  const auto sub = hierarchical_matching_nd(rest, k);
+  for (int x = 0; x < m; x++) {
+    if (matched[x]) continue;
+    for (auto& pr : sub) out.push_back({x * inner + pr.first, pr.second < 0 ? -1 : x * inner + pr.second});
+  }
+  return out;
+}
+
 // ---------------------------------------------------------------------------------------
 // Packing matched pairs into K chunks of `slots` (16) pairs so that, within every chunk,
 // the first-column offsets and the second-column offsets are distinct mod 16 (see the
@@ -454,16 +480,21 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
                                   int max_pieces, bool drop_zero_pairs, SweepTables* out) {
   SweepTables& T = *out;
   T = SweepTables();
-  T.ndim = 2;
+  const bool d3 = geo.ndim == 3;
+  T.ndim = d3 ? 3 : 2;
   T.R = R;
   T.kt = 2 * R + 1;
-  const int kt = T.kt, r1 = Tile2D::R1, r2 = Tile2D::R2, M = Tile2D::M;
+  const int kt = T.kt;
+  const int r1 = d3 ? Tile3D::R1 : Tile2D::R1, r2 = d3 ? Tile3D::R2 : Tile2D::R2, r3 = d3 ? Tile3D::R3 : 1;
+  const int M = d3 ? Tile3D::M : Tile2D::M;
   T.r1 = r1;
   T.r2 = r2;
+  T.r3 = r3;
   T.g = kt + r1 - 1;
   T.mb = kt + r2 - 1;
-  T.kprime = T.g * T.mb;
-  if ((int)wfused.size() != kt * kt) return "fused weight cube has the wrong size";
+  T.mz = d3 ? kt + r3 - 1 : 1;
+  T.kprime = T.g * T.mb * T.mz;
+  if ((int)wfused.size() != (d3 ? kt * kt * kt : kt * kt)) return "fused weight cube has the wrong size";
   T.wfused = wfused;
   T.wfused32.resize(wfused.size());
   double S = 0.0;
@@ -476,13 +507,16 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   T.S_lo = (float)(S - (double)T.S_hi);
 
   // Staircase A' (Sec. 3.1): row rho = s*r1 + tau, column kappa = u*g + c,
-  // A'[rho][kappa] = w[u - s][c - tau] when both differences lie in [0, kt).
+  // A'[rho][kappa] = w[u - s][c - tau] when both differences lie in [0, kt).  3D (a third
+  // crush along z, nested one level deeper): row rho = (q*r2 + s)*r1 + tau, column
+  // kappa = (v*mb + u)*g + c, A'[rho][kappa] = w[v - q][u - s][c - tau].
   const int g = T.g, mb = T.mb, kp = T.kprime;
   auto aval = [&](int rho, int kappa) -> float {
-    int s = rho / r1, tau = rho % r1, u = kappa / g, c = kappa % g;
-    int dy = u - s, dx = c - tau;
-    if (dy < 0 || dy >= kt || dx < 0 || dx >= kt) return 0.f;
-    return T.wfused32[dy * kt + dx];
+    const int tau = rho % r1, s = (rho / r1) % r2, q = rho / (r1 * r2);
+    const int c = kappa % g, u = (kappa / g) % mb, v = kappa / (g * mb);
+    const int dz = v - q, dy = u - s, dx = c - tau;
+    if (dz < 0 || dz >= (d3 ? kt : 1) || dy < 0 || dy >= kt || dx < 0 || dx >= kt) return 0.f;
+    return T.wfused32[(dz * kt + dy) * kt + dx];
   };
   std::vector<char> colnz(kp, 0);
   for (int kap = 0; kap < kp; kap++)
@@ -490,7 +524,7 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
       if (aval(rho, kap) != 0.f) colnz[kap] = 1;
 
   // Structured sparsity conversion (Sec. 3.2).
-  auto pairs = hierarchical_matching(kp, g, kt);
+  auto pairs = d3 ? hierarchical_matching_nd({T.mz, mb, g}, kt) : hierarchical_matching(kp, g, kt);
   std::vector<std::pair<int, int>> kept;
   for (auto& pr : pairs) {
     bool a_nz = colnz[pr.first];
@@ -506,7 +540,13 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   // (py*R2*P + px*R1).  The tile starts G cells before the tile's first output, the patch
   // window R cells before the patch's first output.  A zero column reads its pair partner
   // (any finite value works: its weights are zero).
-  auto off = [&](int col) { return (col / g + geo.G - R) * geo.P + (col % g + geo.G - R); };
+  // 3D: a tile plane holds box_h rows of P words, and the patch window starts R planes
+  // before the patch's first output plane as well.
+  auto off = [&](int col) {
+    const int c = col % g, u = (col / g) % mb, v = col / (g * mb);
+    const int plane = geo.box_h * geo.P;
+    return (d3 ? (v + geo.G - R) * plane : 0) + (u + geo.G - R) * geo.P + (c + geo.G - R);
+  };
   std::vector<std::pair<int, int>> offs;
   for (auto& pr : kept) offs.push_back({off(pr.first), pr.second >= 0 ? off(pr.second) : off(pr.first)});
   std::vector<std::pair<int, int>> offs_free;  // zero partners marked -1: they may read any word
@@ -532,9 +572,10 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   const int half = kpad / 2;
 
   // Weight pieces: w * 2^s = p0 + p1 + p2, each RN-even in the 16-bit word.  FP16 scales
-  // the weights so that the largest is in [0.5, 1) (keeps the pieces out of the subnormal
-  // range); BF16 has FP32's exponent range and uses s = 0.  Three BF16 pieces hold an FP32
-  // weight exactly (3 x 8 significand bits).
+  // the weights so that the largest is in [2^10, 2^11): the third piece of every weight within
+  // a factor 2^10 of the largest then stays a normal FP16 number, and three pieces (3 x 11
+  // significand bits) hold it exactly; BF16 has FP32's exponent range, uses s = 0, and three
+  // BF16 pieces hold an FP32 weight exactly (3 x 8 significand bits).
   if (max_pieces < 1 || max_pieces > 3) return "bad piece count";
   double wmax = 0.0;
   for (float v : T.wfused32) wmax = std::max(wmax, (double)std::fabs(v));
@@ -542,7 +583,7 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   if (word == Word::FP16 && wmax > 0.0) {
     int e;
     std::frexp(wmax, &e);  // wmax = f * 2^e, f in [0.5, 1)
-    s = -e;
+    s = 11 - e;            // largest scaled weight in [2^10, 2^11)
   }
   T.wscale_log2 = s;
   // Compression with 2:4 metadata (Sec. 3.3, Metadata; Sec. 2.1 for sub-2:4 groups).

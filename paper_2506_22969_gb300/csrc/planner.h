@@ -26,6 +26,19 @@ struct Tile2D {
   static constexpr int KCHUNK = 32;   // logical K per tcgen05.mma.sp (kind::f16)
 };
 
+// Geometry of the 3D sweep kernel: a patch is R1 x R2 x R3 = 8 x 4 x 4 outputs (x, y, z),
+// M = 128 rows; a CTA tile is NX x NY x NZ = 8 x 4 x 4 patches = 64 x 16 x 16 outputs,
+// N = 128 columns.
+struct Tile3D {
+  static constexpr int R1 = 8, R2 = 4, R3 = 4;
+  static constexpr int NX = 8, NY = 4, NZ = 4;
+  static constexpr int M = R1 * R2 * R3;
+  static constexpr int N = NX * NY * NZ;
+  static constexpr int TX = NX * R1;  // 64
+  static constexpr int TY = NY * R2;  // 16
+  static constexpr int TZ = NZ * R3;  // 16
+};
+
 // Tables for one sweep kind (t fused steps).
 struct SweepTables {
   int ndim = 2;
@@ -63,6 +76,7 @@ struct PlanGeometry {
   int P = 0;                      // shared-memory tile pitch (floats) = TMA box width
   int box_h = 0;                  // TMA box height
   int64_t tiles_x = 0, tiles_y = 0, tiles_z = 1, num_tiles = 0;
+  int box_d = 1;                  // TMA box depth (3D)
 };
 
 // Composes t steps of the offset-indexed cube w (radius r, ndim axes) into one cube of
@@ -86,10 +100,16 @@ int arrange_pairs(const std::vector<std::pair<int, int>>& pairs, const std::vect
 int pack_pairs_min_repeats(const std::vector<std::pair<int, int>>& pairs, const std::vector<std::pair<int, int>>& offs,
                            int slots, std::vector<int>* order_out, std::vector<int32_t>* lut_out);
 
-// Builds the sweep tables of a 2D stencil (fused cube `wfused` of radius R) for the Tile2D
-// kernel geometry, the ghost width G and tile pitch P of `geo`, and operand encoding `word`.
-// max_pieces: number of 16-bit pieces the weights may use (1..3).  Returns an empty string
-// or an error message.
+// Algorithm 1 applied level by level for a nested staircase (the 3D reading): block pairing
+// at the outermost level (sizes[0] blocks of prod(sizes[1..]) columns, stride
+// max(floor(m/2), k)), matched blocks paired elementwise, recursion into each unmatched
+// block.  For two levels it is hierarchical_matching.
+std::vector<std::pair<int, int>> hierarchical_matching_nd(const std::vector<int>& sizes, int k);
+
+// Builds the sweep tables of a 2D (geo.ndim = 2, Tile2D) or 3D (geo.ndim = 3, Tile3D) stencil
+// (fused cube `wfused` of radius R) for the ghost width G, tile pitch P (and box height of a
+// 3D tile plane) of `geo`, and operand encoding `word`.  max_pieces: number of 16-bit pieces
+// the weights may use (1..3).  Returns an empty string or an error message.
 std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, const PlanGeometry& geo, Word word,
                                   int max_pieces, bool drop_zero_pairs, SweepTables* out);
 

@@ -272,7 +272,7 @@ __device__ __forceinline__ void trace_chunk(bool on, int src, int kc, int ev) {
 struct SmemLayout {
   uint32_t halo_stride, off_b, slot_bytes, off_lut, off_cv, off_bar, total;
   __host__ __device__ explicit SmemLayout(const Sweep2DParams& p) {
-    uint32_t halo = (uint32_t)p.box_h * (uint32_t)p.P * 4u;
+    uint32_t halo = (uint32_t)p.box_d * (uint32_t)p.box_h * (uint32_t)p.P * 4u;
     halo_stride = (halo + 1023u) & ~1023u;
     off_b = halo_stride * kHaloStages;
     slot_bytes = (uint32_t)p.b_pieces * (uint32_t)kPieceBytes;
@@ -295,7 +295,11 @@ constexpr int kGatherWarp0 = 4 + kEpiWarps;                     // the last 16 w
 constexpr int kGatherWarps = kSweepThreads / 32 - kGatherWarp0;  // 16
 constexpr int kItems = 64 / kGatherWarps;                        // patch pairs per gather warp per chunk
 
-template <int FP16, int SPLIT>
+// DIM3 = 0: 2D sweep (Tile2D: 16 x 8 patches, 128 x 128 tiles); DIM3 = 1: 3D sweep (Tile3D:
+// 8 x 4 x 4 patches, 64 x 16 x 16 tiles).  Patch n of a 3D tile, with n = a*16 + h*8 + b, is
+// (px, py, pz) = (4(a&1) + 2h + (b&1), b>>1, a>>1): the two half-warps of a gather warp take
+// patches n and n+8, 16 words apart in x, as in 2D.
+template <int FP16, int SPLIT, int DIM3>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep2d_kernel(const __grid_constant__ CUtensorMap tmap_in, const Sweep2DParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -410,6 +414,18 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   // the next sweep may be scheduled now; its own griddepcontrol.wait orders its grid
   // accesses after this grid's completion
   asm volatile("griddepcontrol.launch_dependents;");
+  // FP16 data scale 2^k (read after the wait: the copy-in wrote max|u0|)
+  float dscale = 1.f, dscale_inv = 1.f;
+  if (FP16 && p.maxabs) {
+    const float bound = 2.f * __uint_as_float(*(const volatile unsigned*)p.maxabs) * p.growth;
+    if (bound > 1e-30f && bound < 3.0e38f) {
+      int e;
+      frexpf(8192.f / bound, &e);  // 8192 / bound = f * 2^e, f in [0.5, 1)
+      const int kk = min(max(e - 1, -60), 60);
+      dscale = ldexpf(1.f, kk);
+      dscale_inv = ldexpf(1.f, -kk);
+    }
+  }
 
   const int ntiles_cta = (p.num_tiles > (int)blockIdx.x) ? (p.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const bool tr = (blockIdx.x == 0) && g_trace_on;
@@ -417,21 +433,30 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      const uint32_t bytes = (uint32_t)p.box_h * (uint32_t)p.P * 4u;
+      const uint32_t bytes = (uint32_t)p.box_d * (uint32_t)p.box_h * (uint32_t)p.P * 4u;
       int issued = 0;
       for (int li = 0; li < ntiles_cta; li++) {
         const int stage = li & 1;
         if (li >= 2 && !mbar_wait(bar(BAR_HEMPTY + stage), ((li >> 1) - 1) & 1, wait_ns, abort_flag, p.status)) break;
         const int tt = (int)blockIdx.x + li * (int)gridDim.x;
-        const int x0 = (tt % p.tiles_x) * 128, y0 = (tt / p.tiles_x) * 128;
         const uint32_t dst = sbase + (uint32_t)stage * L.halo_stride;
         trace(tr, 0, li, 0);
         mbar_expect_tx(bar(BAR_HFULL + stage), bytes);
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-                dst),
-            "l"(&tmap_in), "r"(x0), "r"(y0), "r"(bar(BAR_HFULL + stage))
-            : "memory");
+        if (DIM3) {
+          const int tx = tt % p.tiles_x, ty = (tt / p.tiles_x) % p.tiles_y, tz = tt / (p.tiles_x * p.tiles_y);
+          asm volatile(
+              "cp.async.bulk.tensor.3d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+                  dst),
+              "l"(&tmap_in), "r"(tx * 64), "r"(ty * 16), "r"(tz * 16), "r"(bar(BAR_HFULL + stage))
+              : "memory");
+        } else {
+          const int x0 = (tt % p.tiles_x) * 128, y0 = (tt / p.tiles_x) * 128;
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                  dst),
+              "l"(&tmap_in), "r"(x0), "r"(y0), "r"(bar(BAR_HFULL + stage))
+              : "memory");
+        }
         issued++;
       }
       // the CTA never exits with one of its copies in flight (at most the last two can be)
@@ -511,9 +536,13 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     constexpr int kGroups = 8 / (kEpiWarps / 4);  // 16-column groups per warp
     const int cg0 = ((warp - 4) >> 2) * kGroups;
     const int rho = 32 * q + lane;
-    const int ry = rho >> 4, rx = rho & 15;
+    // row rho of a patch: 2D (ry, rx) = (rho / 16, rho % 16); 3D (rz, ry, rx) = (rho / 32,
+    // rho / 8 % 4, rho % 8)
+    const int rz = DIM3 ? rho >> 5 : 0;
+    const int ry = DIM3 ? (rho >> 3) & 3 : rho >> 4, rx = DIM3 ? rho & 7 : rho & 15;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
     const uint32_t cv_s = sbase + L.off_cv;
+    const float out_scale = p.wscale * dscale_inv;  // undoes the weight and data scales (powers of two)
     const int G = p.out_off;
     const int64_t pitch8 = 8 * p.out_pitch;
     for (int li = 0; li < ntiles_cta; li++) {
@@ -523,12 +552,17 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;");
       trace(tr && warp == 4 && lane == 0, 3, li, 0);
       const int tt = (int)blockIdx.x + li * (int)gridDim.x;
-      const int x0 = (tt % p.tiles_x) * 128, y0 = (tt / p.tiles_x) * 128;
-      // full tiles store without bounds checks; tiles that touch the ghost band of a periodic
-      // padded output also write the images of their band outputs
-      const bool full = (y0 + 128 <= p.H) && (x0 + 128 <= p.W);
-      const bool ghost = p.out_ghost && (y0 < G || y0 + 128 > p.H - G || x0 < G || x0 + 128 > p.W - G);
-      float* obase = p.out + (int64_t)(y0 + G + ry) * p.out_pitch + (x0 + G + rx);
+      const int tx = tt % p.tiles_x, ty = DIM3 ? (tt / p.tiles_x) % p.tiles_y : tt / p.tiles_x;
+      const int x0 = tx * (DIM3 ? 64 : 128), y0 = ty * (DIM3 ? 16 : 128);
+      const int z0 = DIM3 ? (tt / (p.tiles_x * p.tiles_y)) * 16 : 0;
+      // full tiles store without bounds checks; 2D tiles that touch the ghost band of a periodic
+      // padded output also write the images of their band outputs (a 3D sweep's ghost shell
+      // is refreshed by a separate kernel)
+      const bool full = DIM3 ? (z0 + 16 <= p.D && y0 + 16 <= p.H && x0 + 64 <= p.W)
+                             : ((y0 + 128 <= p.H) && (x0 + 128 <= p.W));
+      const bool ghost = !DIM3 && p.out_ghost && (y0 < G || y0 + 128 > p.H - G || x0 < G || x0 + 128 > p.W - G);
+      float* obase = p.out + (int64_t)(z0 + G + rz) * (DIM3 ? p.out_plane : 0) + (int64_t)(y0 + G + ry) * p.out_pitch +
+                     (x0 + G + rx);
 #pragma unroll 1
       for (int cg = cg0; cg < cg0 + kGroups; cg++) {
         uint32_t v[16];
@@ -548,11 +582,23 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           c[4 * k4 + 3] = c4.w;
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        // columns cg*16 .. +15 are patches (py, px) = (cg/4*8 + j%8, (2cg + j/8) % 8)
-        const int py0 = (cg >> 2) << 3, px0 = (2 * cg) & 7;
         float val[16];
 #pragma unroll
-        for (int j = 0; j < 16; j++) val[j] = fmaf(c[j], p.S_lo, fmaf(c[j], p.S_hi, __uint_as_float(v[j]) * p.wscale));
+        for (int j = 0; j < 16; j++) val[j] = fmaf(c[j], p.S_lo, fmaf(c[j], p.S_hi, __uint_as_float(v[j]) * out_scale));
+        if (DIM3) {
+          // columns cg*16 + j are patches (px, py, pz) = (4(cg&1) + 2(j/8) + (j&1), (j&7)/2, cg/2)
+          const int pz = cg >> 1, pxh = (cg & 1) << 2;
+          const int64_t zoff = (int64_t)pz * 4 * p.out_plane;
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const int px = pxh | ((j >> 3) << 1) | (j & 1), py = (j & 7) >> 1;
+            const int64_t o = zoff + (int64_t)py * 4 * p.out_pitch + px * 8;
+            if (full || (z0 + pz * 4 + rz < p.D && y0 + py * 4 + ry < p.H && x0 + px * 8 + rx < p.W)) obase[o] = val[j];
+          }
+          continue;
+        }
+        // columns cg*16 .. +15 are patches (py, px) = (cg/4*8 + j%8, (2cg + j/8) % 8)
+        const int py0 = (cg >> 2) << 3, px0 = (2 * cg) & 7;
         if (full) {
 #pragma unroll
           for (int j = 0; j < 16; j++) obase[(int64_t)(py0 + (j & 7)) * pitch8 + (px0 + (j >> 3)) * 16] = val[j];
@@ -603,9 +649,15 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     for (int i = 0; i < kItems; i++) {
       const int pp = gw + kGatherWarps * i;
       const int n = (pp >> 3) * 16 + (pp & 7) + 8 * h;
-      const int px = (n >> 3) & 7, py = ((n >> 6) << 3) + (n & 7);
       n_i[i] = n;
-      base_i[i] = 4 * (py * 8 * P + px * 16);
+      if (DIM3) {
+        const int a = n >> 4, b = n & 7;
+        const int px = ((a & 1) << 2) | (h << 1) | (b & 1), py = b >> 1, pz = a >> 1;
+        base_i[i] = 4 * (pz * 4 * p.box_h * P + py * 4 * P + px * 8);
+      } else {
+        const int px = (n >> 3) & 7, py = ((n >> 6) << 3) + (n & 7);
+        base_i[i] = 4 * (py * 8 * P + px * 16);
+      }
       soff_i[i] = (uint32_t)((n >> 3) * kSBO + (n & 7) * 16) + pairoff;
     }
     const uint32_t lut_sa = sbase + L.off_lut + 8u * (uint32_t)pl;
@@ -619,9 +671,23 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 #pragma unroll
       for (int i = 0; i < kItems; i++) {
         ba[i] = tile_s + (uint32_t)base_i[i];
-        // the patch constant: the input value at the patch centre (row 4, column 8 of its
-        // 8 x 16 outputs), which keeps |u - c| small over the patch's whole stencil window
-        c_i[i] = lds_f32(ba[i] + 4u * (uint32_t)((G + 4) * P + G + 8));
+        // the patch constant: the mean of the 8 inputs in the middle of the patch's outputs
+        // (2D rows 3-4 x columns 6-9 of its 8 x 16, 3D the central 2 x 2 x 2 of its 4 x 4 x 8).
+        // Any c gives the same sum (sum w (u - c) + c sum w); the MMAs round their FP32
+        // partial sums, so c should keep |u - c| small: near the local value for smooth data
+        // with an offset, near the local mean (not one sample of it) for rough zero-mean data
+        const uint32_t m0 = ba[i] + 4u * (uint32_t)(DIM3 ? (G + 1) * p.box_h * P + (G + 1) * P + G + 3
+                                                         : (G + 3) * P + G + 6);
+        const uint32_t row = 4u * (uint32_t)P, plane = 4u * (uint32_t)(p.box_h * P);
+        float cs;
+        if (DIM3)
+          cs = ((lds_f32(m0) + lds_f32(m0 + 4u)) + (lds_f32(m0 + row) + lds_f32(m0 + row + 4u))) +
+               ((lds_f32(m0 + plane) + lds_f32(m0 + plane + 4u)) +
+                (lds_f32(m0 + plane + row) + lds_f32(m0 + plane + row + 4u)));
+        else
+          cs = ((lds_f32(m0) + lds_f32(m0 + 4u)) + (lds_f32(m0 + 8u) + lds_f32(m0 + 12u))) +
+               ((lds_f32(m0 + row) + lds_f32(m0 + row + 4u)) + (lds_f32(m0 + row + 8u) + lds_f32(m0 + row + 12u)));
+        c_i[i] = 0.125f * cs;
       }
       // the patch constants go to a two-slot area of their own, so that building B'' for this
       // tile never waits for the epilogue that is draining the accumulator
@@ -669,8 +735,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         const uint32_t bs = sbase + L.off_b + slot * L.slot_bytes;
 #pragma unroll
         for (int i = 0; i < kItems; i++) {
-          const float da = va[i] - c_i[i];
-          const float db = vb[i] - c_i[i];
+          const float da = (va[i] - c_i[i]) * dscale;
+          const float db = (vb[i] - c_i[i]) * dscale;
           const uint32_t hi = pack2(da, db, FP16);
           sts_u32(bs + soff_i[i], hi);
           if (SPLIT) {
@@ -786,8 +852,10 @@ cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p_in
     if (need > (size_t)L.off_lut) return cudaErrorInvalidConfiguration;
   }
   const size_t smem = sweep2d_smem_bytes(p);
-  auto kern = p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1> : sweep2d_kernel<1, 0>)
-                     : (p.b_pieces > 1 ? sweep2d_kernel<0, 1> : sweep2d_kernel<0, 0>);
+  auto kern = p.dim3 ? (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 1> : sweep2d_kernel<1, 0, 1>)
+                              : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 1> : sweep2d_kernel<0, 0, 1>))
+                     : (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 0> : sweep2d_kernel<1, 0, 0>)
+                              : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 0> : sweep2d_kernel<0, 0, 0>));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;

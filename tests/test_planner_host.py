@@ -108,18 +108,18 @@ def test_planner_tables_against_oracle(lib, oracle_mod, shape, r, recipe, t, dty
     split = dtype.endswith("split")
     fp16 = dtype.startswith("fp16")
     rnd = _fp16 if fp16 else _bf16
-    s = -int(np.frexp(np.max(np.abs(wf32)))[1]) if fp16 else 0  # FP16 pieces hold w * 2^s
+    s = 11 - int(np.frexp(np.max(np.abs(wf32)))[1]) if fp16 else 0  # FP16 pieces hold w * 2^s
     sc = 2.0 ** s
     dense_hi = morph.decompress_2_4(tb["a_hi"].astype(np.float64), tb["a_idx"])
     dense_lo = morph.decompress_2_4(tb["a_lo"].astype(np.float64), tb["a_idx"])
     assert morph.satisfies_2_4(dense_hi) and morph.satisfies_2_4(dense_hi + dense_lo)
     Ap = morph.apply_permutation(A, list(order))
     np.testing.assert_array_equal(dense_hi, rnd(Ap * sc) / sc)
-    # weight pieces: split operands use three (two for a fused sweep that needs the TMEM for a
-    # second accumulator), single-word operands two; one MMA term per piece, plus one for the
-    # data's low part with split operands
+    # weight pieces: BF16 split operands use three (two for a fused sweep that needs the TMEM
+    # for a second accumulator), FP16 split and single-word operands two; one MMA term per
+    # piece, plus one for the data's low part with split operands
     pieces = info.mma_terms - (1 if split else 0)
-    assert pieces in (1, 2, 3) and (pieces == 3 or not split or t >= 2)
+    assert pieces in (1, 2, 3) and (pieces == 3 or not split or t >= 2 or fp16)
     if pieces == 3 and not fp16:
         # three BF16 pieces hold every FP32 weight exactly
         np.testing.assert_array_equal(dense_hi + dense_lo, Ap)
@@ -243,3 +243,101 @@ def test_autotune_plan_takes_the_deepest_depth_that_fits(lib):
     w3 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=2)
     p3 = binding.Plan(w3, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=0)
     assert p3.info().fusion_depth == 1
+
+
+def _oracle_order_3d(wf, k, r1, r2, r3):
+    """The 3D reading: nested staircase A' and Algorithm 1 applied level by level."""
+    A = morph.crushed_weights_3d(wf, r1, r2, r3)
+    g, mb, mz = k + r1 - 1, k + r2 - 1, k + r3 - 1
+    nz = np.any(A != 0, axis=0)
+    order = []
+    for a, b in morph.hierarchical_matching_nd([mz, mb, g], k):
+        if not nz[a] and (b == ZERO or not nz[b]):
+            continue
+        order.extend([a, b])
+    while len(order) % 32:
+        order.append(ZERO)
+    return A, np.array(order)
+
+
+@pytest.mark.parametrize("shape,recipe,dtype", [("box", "random", "bf16"), ("star", "random", "bf16_split"),
+                                                ("box", "random", "fp16")])
+def test_planner_tables_3d_against_oracle(lib, shape, recipe, dtype):
+    """3D plans (Tile3D: 8 x 4 x 4 patches): same pair set as the oracle's level-by-level
+    Algorithm 1, 2:4 holds, and the decompressed A'' un-permutes to the oracle's A'."""
+    w = inputs.stencil_weights(shape, 3, 1, recipe, seed=7)
+    plan = binding.Plan(w, (40, 36, 72), dtype=dtype, bc="periodic", fusion_depth=1, shape=shape)
+    info = plan.info()
+    tb = plan.tables()
+    wf32 = tb["fused_w"].astype(np.float32).astype(np.float64)
+    np.testing.assert_array_equal(wf32, w.astype(np.float64))
+    A, alg = _oracle_order_3d(wf32, 3, 8, 4, 4)
+    assert info.r1 == 8 and info.r2 == 4 and info.r3 == 4 and info.kprime == A.shape[1]
+    order = tb["order"]
+
+    def pairset(o):
+        return sorted(tuple(sorted((int(o[2 * i]), int(o[2 * i + 1])))) for i in range(len(o) // 2)
+                      if not (o[2 * i] == ZERO and o[2 * i + 1] == ZERO))
+    assert pairset(order) == pairset(alg) and info.kpad == len(alg)
+    dense = morph.decompress_2_4(tb["a_hi"].astype(np.float64) + tb["a_lo"], tb["a_idx"])
+    assert morph.satisfies_2_4(dense)
+    Ap = morph.apply_permutation(A, list(order))
+    if dtype == "bf16_split":
+        np.testing.assert_array_equal(dense, Ap)  # three BF16 pieces: exact
+    else:
+        assert np.max(np.abs(dense - Ap)) <= 2.0 ** -16 * np.max(np.abs(A))
+
+
+def _emulate_sweep_3d(plan, tb, u, bc, dense):
+    """Host emulation of one 3D sweep through the planner's LUT: padded grid -> halo boxes
+    (64+2G) x (16+2G) x (16+2G) -> B'' gathered by LUT -> dense A'' @ B'' -> outputs by the
+    patch map of the 3D kernel."""
+    info = plan.info()
+    D, H, W = u.shape
+    G, P, bh = info.ghost, info.tile_pitch, info.tile_rows
+    bd = 16 + 2 * G
+    Wp = (W + 2 * G + 3) // 4 * 4
+    up = np.zeros((D + 2 * G, H + 2 * G, Wp))
+    zz, yy, xx = np.mgrid[-G:D + G, -G:H + G, -G:W + G]
+    if bc == "periodic":
+        up[:, :, :W + 2 * G] = u[zz % D, yy % H, xx % W]
+    else:
+        inside = (zz >= 0) & (zz < D) & (yy >= 0) & (yy < H) & (xx >= 0) & (xx < W)
+        up[:, :, :W + 2 * G] = np.where(inside, u[np.clip(zz, 0, D - 1), np.clip(yy, 0, H - 1),
+                                                  np.clip(xx, 0, W - 1)], 0.0)
+    out = np.full((D, H, W), np.nan)
+    lut = tb["lut"]
+    for tz in range((D + 15) // 16):
+        for ty in range((H + 15) // 16):
+            for tx in range((W + 63) // 64):
+                tile = np.zeros((bd, bh, P))
+                blk = up[tz * 16:tz * 16 + bd, ty * 16:ty * 16 + bh, tx * 64:tx * 64 + P]
+                tile[:blk.shape[0], :blk.shape[1], :blk.shape[2]] = blk
+                flat = tile.ravel()
+                for n in range(128):
+                    a, h, b = n >> 4, (n >> 3) & 1, n & 7
+                    px, py, pz = ((a & 1) << 2) | (h << 1) | (b & 1), b >> 1, a >> 1
+                    base = pz * 4 * bh * P + py * 4 * P + px * 8
+                    col = dense @ flat[base + lut]
+                    for rho in range(128):
+                        z = tz * 16 + pz * 4 + (rho >> 5)
+                        y = ty * 16 + py * 4 + ((rho >> 3) & 3)
+                        x = tx * 64 + px * 8 + (rho & 7)
+                        if z < D and y < H and x < W:
+                            out[z, y, x] = col[rho]
+    return out
+
+
+@pytest.mark.parametrize("bc,shape", [("periodic", "box"), ("dirichlet", "star")])
+def test_lut_emulation_3d_reproduces_oracle_step(lib, oracle_mod, bc, shape):
+    """Bit-level check of the 3D tables the kernel consumes: with dyadic weights and data
+    the emulated sweep equals one oracle step exactly."""
+    mask = inputs.stencil_mask(shape, 3, 1)
+    w = np.where(mask, np.arange(1, 28).reshape(3, 3, 3) / 256.0, 0.0).astype(np.float32)
+    u = np.random.default_rng(5).integers(-8, 9, size=(20, 18, 70)).astype(np.float64) / 8.0
+    plan = binding.Plan(w, u.shape, dtype="bf16", bc=bc, fusion_depth=1, shape=shape)
+    tb = plan.tables()
+    dense = morph.decompress_2_4(tb["a_hi"].astype(np.float64) + tb["a_lo"], tb["a_idx"])
+    got = _emulate_sweep_3d(plan, tb, u, bc, dense)
+    ref = oracle_mod.run(u, w.astype(np.float64), bc, 1)
+    np.testing.assert_array_equal(got, ref)
