@@ -479,7 +479,8 @@ def _rel_l2_gpu(binding, x, ref):
 def suite_mode():
     """Configs C1, C3, C4a/b: GStencil/s of the sparse path (single and split, fusion depth
     autotuned) and of the plain FP32 direct kernel, with rel-L2 against the FP64 oracle (C1:
-    full grid; C3: sampled points) or against the FP32 direct result (C4)."""
+    full grid; C3: sampled points, plus the whole grid against the FP32 direct result) or
+    against the FP32 direct result (C4)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -499,17 +500,28 @@ def suite_mode():
         ref_gpu = torch.empty_like(x)
         ms_d, _ = _time_runs(lambda: binding.direct_run(w, x, ref_gpu, work, T, bc=bc), 2, 1, flush)
         line["fp32_direct_gstencil_s"] = pts / ms_d / 1e6
+        sample, sample_ref = None, None
         if cfg["ndim"] == 3:
+            # 3D: sampled points against the FP64 oracle's dependence cones, and the whole grid
+            # against the FP32 direct kernel
             rng = np.random.default_rng(0)
             sample = [tuple(int(rng.integers(0, d)) for d in dims) for _ in range(6)]
-            ref = np.array([oracle.point(u, w, bc, T, p) for p in sample])
-            got = ref_gpu.cpu().numpy().astype(np.float64)
-            vals = np.array([got[p] for p in sample])
-            line["fp32_direct_rel_l2_sampled_vs_oracle"] = float(np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2)))
-            line["sparse"] = "not built for 3D grids (FP32 CUDA-core kernel only)"
-            print(json.dumps(line), flush=True)
-            continue
-        dtypes = ("fp16",) if name == "heat2d_512" else ("bf16", "bf16_split")
+            u64 = u.astype(np.float64)
+            sample_ref = np.array([oracle.point(u64, w, bc, T, p) for p in sample])
+            del u64
+
+            def sampled_l2(t):
+                got = t.cpu().numpy()
+                vals = np.array([float(got[p]) for p in sample])
+                return float(np.sqrt(np.sum((vals - sample_ref) ** 2) / np.sum(sample_ref ** 2)))
+
+            line["fp32_direct_rel_l2_sampled_vs_oracle"] = sampled_l2(ref_gpu)
+        if name == "heat2d_512":
+            dtypes = ("fp16",)
+        elif cfg["ndim"] == 3:
+            dtypes = ("fp16", "bf16", "fp16_split", "bf16_split")
+        else:
+            dtypes = ("bf16", "bf16_split")
         full_ref = oracle.run(u, w, bc, T) if name == "heat2d_512" else None
         for dt in dtypes:
             try:
@@ -521,6 +533,10 @@ def suite_mode():
             ms, med = _time_runs(lambda: plan.run(x, y, T), 3, 1, flush)
             line[f"{dt}_sparse_gstencil_s"] = pts / ms / 1e6
             line[f"{dt}_fusion_depth"] = plan.info().fusion_depth
+            if dt.endswith("split"):
+                line[f"{dt}_low_accumulator"] = plan.info().low_accumulator
+            if sample is not None:
+                line[f"{dt}_rel_l2_sampled_vs_oracle"] = sampled_l2(y)
             if full_ref is not None:
                 l2, linf = oracle.rel_errors(y.cpu().numpy().astype(np.float64), full_ref)
                 line[f"{dt}_rel_l2_vs_oracle"] = l2

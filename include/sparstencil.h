@@ -74,6 +74,7 @@ typedef struct {
   int tile_rows;       /* rows of the halo tile (TMA box height) */
   int bank_conflicts;  /* residue repeats left by the planner's chunk packing (0: the B'' gather
                           reads shared memory without bank conflicts) */
+  int low_accumulator; /* 1: split terms after A_hi B_hi accumulate separately (see below) */
 } sparstencil_plan_info;
 
 /* Builds a plan for `shape` stencils of radius `radius` on an ndim grid of extents dims.
@@ -91,6 +92,22 @@ typedef struct {
 sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const float* weights, int ndim,
                                     const int64_t* dims, sparstencil_dtype dtype, sparstencil_boundary bc,
                                     int fusion_depth, sparstencil_plan_t* out_plan);
+
+/* Split dtypes only: enable != 0 sends the low-order MMA terms (A_hi B_lo, A_lo B_hi, ...) to
+ * a TMEM accumulator of their own, which the epilogue adds in FP32 to the A_hi B_hi one.
+ * Every tensor-core MMA rounds its FP32 result once; with one accumulator each low-order term
+ * costs a rounding at the magnitude of the whole partial sum, with two only the A_hi B_hi
+ * chain does (about 3x less error on rough data, e.g. zero-mean 3D grids over 50 steps).
+ * A tile then takes 256 TMEM columns, so the next tile's MMAs no longer overlap this tile's
+ * write-back; BF16 split keeps three weight pieces only where they fit beside them (with two
+ * pieces its weight rounding, 2^-17, outweighs what the second accumulator saves).
+ * Default: on for SPST_FP16_SPLIT plans where it fits (their operands hold 22 bits, so the
+ * MMA roundings dominate), off otherwise.
+ * Must be called before the plan's first run (it rebuilds the host tables).
+ * Errors: SPST_ERR_INVALID (null plan, single-word dtype, plan already ran),
+ * SPST_ERR_UNSUPPORTED (the plan's fusion depth does not fit in TMEM this way; the plan is
+ * left unchanged).  Host only. */
+sparstencil_status sparstencil_plan_set_low_accumulator(sparstencil_plan_t plan, int enable);
 
 /* Runs `timesteps` stencil steps: out = S^timesteps in (Sec. 2.2), on `stream`.
  *   in, out: device FP32 grids of prod(dims) elements, caller-owned, must not alias;

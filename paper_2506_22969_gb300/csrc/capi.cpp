@@ -77,9 +77,12 @@ struct DeviceTables {
 bool is_split(sparstencil_dtype d) { return d == SPST_FP16_SPLIT || d == SPST_BF16_SPLIT; }
 
 // TMEM columns: accumulators (128 each) + A'' pieces + metadata (8-column pairs of chunks).
-// Two accumulators when they fit in the 512 columns, else one, else 0 (does not fit).
-int tmem_accumulators(const SweepTables& T) {
+// Returns the tile buffers that fit in the 512 columns: two accumulators when they fit, else
+// one, else 0 (does not fit); with the low-order accumulator (lo) a tile takes 256 columns
+// and there is at most one buffer.
+int tmem_accumulators(const SweepTables& T, bool lo = false) {
   const int rest = T.a_pieces * (T.kpad / 4) + 8 * ((T.kpad / 32 + 1) / 2);
+  if (lo) return 256 + rest <= 512 ? 1 : 0;
   if (256 + rest <= 512) return 2;
   if (128 + rest <= 512) return 1;
   return 0;
@@ -96,6 +99,7 @@ struct sparstencil_plan_s {
   sparstencil_dtype dtype;
   sparstencil_boundary bc;
   int requested_t = 1, t = 1, t_max = 1;
+  bool lo_acc = false;  // split operands: low-order MMA terms in an accumulator of their own
   bool autotune_pending = false;  // fusion_depth 0: t is chosen by timing at the first run
   std::vector<double> w64;  // input weights (FP32 values promoted exactly)
   PlanGeometry geo;
@@ -145,17 +149,22 @@ std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
   // while the weight rounding (<= 2^-17 relative per fused weight) is shared by t steps;
   // measured on the periodic Fourier closed form over 100 steps at t = 3 the rel-L2 error stays
   // below 1e-6.
+  // With the low-order accumulator a tile's two accumulators take 256 columns; three BF16
+  // pieces are kept when the rest fits beside them, else two.
   const int pieces = (is_split(p->dtype) && word_of(p->dtype) == spst::Word::BF16) ? 3 : 2;
   std::string err = spst::build_sweep_tables_2d(wf, depth * p->radius, p->geo, word_of(p->dtype), pieces, true, out);
   if (!err.empty()) return err;
-  if (pieces == 3 && depth >= 2 && tmem_accumulators(*out) < 2) {
+  const bool retry = p->lo_acc ? tmem_accumulators(*out, true) == 0 : (depth >= 2 && tmem_accumulators(*out) < 2);
+  if (pieces == 3 && retry) {
     SweepTables two;
     err = spst::build_sweep_tables_2d(wf, depth * p->radius, p->geo, word_of(p->dtype), 2, true, &two);
     if (!err.empty()) return err;
-    if (tmem_accumulators(two) == 2) *out = std::move(two);
+    if (tmem_accumulators(two, p->lo_acc) == (p->lo_acc ? 1 : 2)) *out = std::move(two);
   }
   out->t = depth;
-  if (tmem_accumulators(*out) == 0) return "stencil too wide for TMEM (kpad " + std::to_string(out->kpad) + ")";
+  if (tmem_accumulators(*out, p->lo_acc) == 0)
+    return std::string("stencil too wide for TMEM (kpad ") + std::to_string(out->kpad) +
+           (p->lo_acc ? ", with the low-order accumulator)" : ")");
   return "";
 }
 
@@ -348,7 +357,8 @@ spst::Sweep2DParams sweep_params(sparstencil_plan_t p, const SweepTables& T, con
     prm.term_a[prm.nterms] = pc;
     prm.term_b[prm.nterms++] = 0;
   }
-  prm.nacc = tmem_accumulators(T);
+  prm.nacc = tmem_accumulators(T, p->lo_acc);
+  prm.lo_acc = p->lo_acc ? 1 : 0;
   prm.fp16 = word_of(p->dtype) == spst::Word::FP16 ? 1 : 0;
   prm.wscale = std::ldexp(1.0f, -T.wscale_log2);
   prm.lut = dt.lut;
@@ -719,9 +729,37 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
     if (err.empty() || fusion_depth != 0) break;
   }
   if (!err.empty()) return fail(SPST_ERR_UNSUPPORTED, err);
+  // FP16 split operands carry 22 significant bits of data and weights, so the roundings of
+  // the MMA chain dominate their error: they take the low-order accumulator where it fits
+  if (dtype == SPST_FP16_SPLIT) {
+    p->lo_acc = true;
+    SweepTables T;
+    if (build_tables(p.get(), p->t, &T).empty())
+      p->full = std::move(T);
+    else
+      p->lo_acc = false;
+  }
   p->autotune_pending = fusion_depth == 0 && p->t_max > 1;
   p->planner_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out_plan = p.release();
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_plan_set_low_accumulator(sparstencil_plan_t plan, int enable) {
+  if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
+  if (enable && !is_split(plan->dtype)) return fail(SPST_ERR_INVALID, "the low-order accumulator needs a split dtype");
+  if (!plan->dev_tables.empty()) return fail(SPST_ERR_INVALID, "set the accumulator mode before the plan's first run");
+  if ((enable != 0) == plan->lo_acc) return SPST_OK;
+  const bool old = plan->lo_acc;
+  plan->lo_acc = enable != 0;
+  SweepTables T;
+  const std::string err = build_tables(plan, plan->t, &T);
+  if (!err.empty()) {
+    plan->lo_acc = old;
+    return fail(SPST_ERR_UNSUPPORTED, err);
+  }
+  plan->full = std::move(T);
+  plan->rem.clear();
   return SPST_OK;
 }
 
@@ -903,6 +941,7 @@ sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_i
   info->tile_pitch = plan->geo.P;
   info->tile_rows = plan->geo.box_h;
   info->bank_conflicts = plan->full.bank_conflicts;
+  info->low_accumulator = plan->lo_acc ? 1 : 0;
   return SPST_OK;
 }
 

@@ -159,43 +159,45 @@ __device__ __forceinline__ void commit_elected(uint32_t bar) {
       : "memory");
 }
 
-// One K chunk's MMAs (1 to 4 terms: A piece x B piece, all into the accumulator at d) and
-// the commit that frees the chunk's B'' slot, issued by one elected lane of a converged warp
-// in a single block.  en: accumulate onto d for the first term (0 for the tile's first chunk).
-#define SPST_MMA_SP(A, B, P) " @e tcgen05.mma.sp.cta_group::1.kind::f16 [%0], [" A "], " B ", [%9], %10, " P ";\n"
+// One K chunk's MMAs (1 to 4 terms: A piece x B piece) and the commit that frees the chunk's
+// B'' slot, issued by one elected lane of a converged warp in a single block.  The first term
+// goes to the accumulator at d, the others to the one at d1 (d1 = d, or the low-order
+// accumulator); en / en1: accumulate onto d / d1 for the first term that writes each (0 for
+// the tile's first chunk).
+#define SPST_MMA_SP(D, A, B, P) " @e tcgen05.mma.sp.cta_group::1.kind::f16 [" D "], [" A "], " B ", [%9], %10, " P ";\n"
 #define SPST_COMMIT " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%12];\n"
-__device__ __forceinline__ void issue_chunk(int nterms, uint32_t d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                            uint64_t b0, uint64_t b1, uint64_t b2, uint64_t b3, uint32_t meta,
-                                            uint32_t idesc, uint32_t en, uint32_t bar) {
+#define SPST_PREDS \
+  "{\n .reg .pred e, q, q1, t;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %11, 0;\n setp.ne.b32 q1, %14, 0;\n" \
+  " setp.eq.b32 t, %11, %11;\n"
+__device__ __forceinline__ void issue_chunk(int nterms, uint32_t d, uint32_t d1, uint32_t a0, uint32_t a1, uint32_t a2,
+                                            uint32_t a3, uint64_t b0, uint64_t b1, uint64_t b2, uint64_t b3, uint32_t meta,
+                                            uint32_t idesc, uint32_t en, uint32_t en1, uint32_t bar) {
 #define SPST_CHUNK_OPERANDS                                                                                   \
   "r"(d), "r"(a0), "r"(a1), "r"(a2), "r"(a3), "l"(b0), "l"(b1), "l"(b2), "l"(b3), "r"(meta), "r"(idesc), "r"(en), \
-      "r"(bar)
+      "r"(bar), "r"(d1), "r"(en1)
   switch (nterms) {
     case 1:
-      asm volatile("{\n .reg .pred e, q, t;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %11, 0;\n"
-                   " setp.eq.b32 t, %11, %11;\n" SPST_MMA_SP("%1", "%5", "q") SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS
-                   : "memory");
+      asm volatile(SPST_PREDS SPST_MMA_SP("%0", "%1", "%5", "q") SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS : "memory");
       break;
     case 2:
-      asm volatile("{\n .reg .pred e, q, t;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %11, 0;\n"
-                   " setp.eq.b32 t, %11, %11;\n" SPST_MMA_SP("%1", "%5", "q") SPST_MMA_SP("%2", "%6", "t")
+      asm volatile(SPST_PREDS SPST_MMA_SP("%0", "%1", "%5", "q") SPST_MMA_SP("%13", "%2", "%6", "q1")
                        SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS
                    : "memory");
       break;
     case 3:
-      asm volatile("{\n .reg .pred e, q, t;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %11, 0;\n"
-                   " setp.eq.b32 t, %11, %11;\n" SPST_MMA_SP("%1", "%5", "q") SPST_MMA_SP("%2", "%6", "t")
-                       SPST_MMA_SP("%3", "%7", "t") SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS
+      asm volatile(SPST_PREDS SPST_MMA_SP("%0", "%1", "%5", "q") SPST_MMA_SP("%13", "%2", "%6", "q1")
+                       SPST_MMA_SP("%13", "%3", "%7", "t") SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS
                    : "memory");
       break;
     default:
-      asm volatile("{\n .reg .pred e, q, t;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %11, 0;\n"
-                   " setp.eq.b32 t, %11, %11;\n" SPST_MMA_SP("%1", "%5", "q") SPST_MMA_SP("%2", "%6", "t")
-                       SPST_MMA_SP("%3", "%7", "t") SPST_MMA_SP("%4", "%8", "t") SPST_COMMIT "}" ::SPST_CHUNK_OPERANDS
+      asm volatile(SPST_PREDS SPST_MMA_SP("%0", "%1", "%5", "q") SPST_MMA_SP("%13", "%2", "%6", "q1")
+                       SPST_MMA_SP("%13", "%3", "%7", "t") SPST_MMA_SP("%13", "%4", "%8", "t") SPST_COMMIT
+                   "}" ::SPST_CHUNK_OPERANDS
                    : "memory");
       break;
   }
 #undef SPST_CHUNK_OPERANDS
+#undef SPST_PREDS
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi, int fp16) {
@@ -371,7 +373,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t a_col = 128u * (uint32_t)nacc;  // accumulators first, then A'' pieces, then metadata
+  // accumulators first (nacc of them, each 128 columns, or 256 with the low-order accumulator
+  // right after the main one), then the A'' pieces, then the metadata
+  const uint32_t acc_stride = p.lo_acc ? 256u : 128u;
+  const uint32_t a_col = acc_stride * (uint32_t)nacc;
   const uint32_t meta_col = a_col + (uint32_t)(pieces * acols);
 
   if (warp >= 4 && warp < 8) {
@@ -495,7 +500,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       if (use > 0 && !warp_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       trace(tr && lane == 0, 1, li, 0);
-      const uint32_t dcol = tmem + (uint32_t)(acc * 128);
+      const uint32_t dcol = tmem + (uint32_t)acc * acc_stride;
+      const uint32_t dcol1 = p.lo_acc ? dcol + 128u : dcol;
       for (int kc = 0; kc < p.kchunks; kc++) {
         const uint32_t slot = mslot, su = mphase;
         if (++mslot == (uint32_t)p.nslots) {
@@ -516,8 +522,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         const uint64_t b1 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[1]);
         const uint64_t b2 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[2]);
         const uint64_t b3 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[3]);
-        issue_chunk(nterms, dcol, a_term[0] + a8, a_term[1] + a8, a_term[2] + a8, a_term[3] + a8, b0, b1, b2, b3, meta,
-                    idesc_kc, kc > 0 ? 1u : 0u, bar(BAR_BEMPTY + slot));
+        issue_chunk(nterms, dcol, dcol1, a_term[0] + a8, a_term[1] + a8, a_term[2] + a8, a_term[3] + a8, b0, b1, b2, b3,
+                    meta, idesc_kc, kc > 0 ? 1u : 0u, (kc > 0 || !p.lo_acc) ? 1u : 0u, bar(BAR_BEMPTY + slot));
         trace_chunk(tr && li == 1 && lane == 0, 2, kc, 1);
       }
       if (!ok) break;
@@ -566,11 +572,24 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 #pragma unroll 1
       for (int cg = cg0; cg < cg0 + kGroups; cg++) {
         uint32_t v[16];
+        const uint32_t acc_addr = lane_addr + (uint32_t)acc * acc_stride + (uint32_t)(cg * 16);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(lane_addr + (uint32_t)(acc * 128 + cg * 16)));
+            : "r"(acc_addr));
+        if (SPLIT && p.lo_acc) {
+          // the low-order accumulator, added in FP32 (RN) to the main one
+          uint32_t l[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7]),
+                "=r"(l[8]), "=r"(l[9]), "=r"(l[10]), "=r"(l[11]), "=r"(l[12]), "=r"(l[13]), "=r"(l[14]), "=r"(l[15])
+              : "r"(acc_addr + 128u));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int j = 0; j < 16; j++) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(l[j]));
+        }
         float c[16];
         const uint32_t ca = cv_s + (uint32_t)((li & 1) * 128 + cg * 16) * 4u;
 #pragma unroll

@@ -245,6 +245,44 @@ def test_autotune_plan_takes_the_deepest_depth_that_fits(lib):
     assert p3.info().fusion_depth == 1
 
 
+def test_low_accumulator_setting(lib):
+    """The low-order accumulator: split dtypes only, before the first run; a tile then takes
+    256 TMEM columns, so BF16 split keeps three weight pieces only where they fit beside it,
+    and a plan whose tables do not fit is refused and left as it was."""
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
+    single = binding.Plan(w, (256, 256), dtype="bf16", fusion_depth=1)
+    with pytest.raises(binding.SparStencilError) as e:
+        single.set_low_accumulator(True)
+    assert e.value.code == 1 and single.info().low_accumulator == 0
+    # box 3x3 at t = 1: three BF16 pieces (3 * 48 + 8 * 2 columns) fit beside two accumulators
+    p1 = binding.Plan(w, (256, 256), dtype="bf16_split", fusion_depth=1, low_accumulator=True)
+    assert p1.info().low_accumulator == 1 and p1.info().mma_terms == 4
+    # box 3x3 at t = 3 (kpad 320): three pieces would need 3 * 80 + 40 + 256 > 512 columns
+    p3 = binding.Plan(w, (512, 512), dtype="bf16_split", fusion_depth=3)
+    assert p3.info().mma_terms == 3
+    p3.set_low_accumulator(True)
+    assert p3.info().low_accumulator == 1 and p3.info().mma_terms == 3
+    p3.set_low_accumulator(False)
+    assert p3.info().low_accumulator == 0
+    # a 7x7 box at t = 1 (K 480 after padding) leaves no room for the second accumulator
+    w7 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=2)
+    p7 = binding.Plan(w7, (512, 512), dtype="fp16_split", fusion_depth=1)
+    kpad = p7.info().kpad
+    if 256 + 2 * (kpad // 4) + 8 * ((kpad // 32 + 1) // 2) > 512:
+        with pytest.raises(binding.SparStencilError) as e:
+            p7.set_low_accumulator(True)
+        assert e.value.code == 2 and p7.info().low_accumulator == 0
+    # FP16 split plans take it by default where it fits (3D radius 1, two pieces); it can be
+    # switched off before the first run
+    for shape in ("star", "box"):
+        w3 = inputs.stencil_weights(shape, 3, 1, "random", seed=3)
+        p = binding.Plan(w3, (64, 64, 128), dtype="fp16_split", fusion_depth=1, shape=shape)
+        assert p.info().low_accumulator == 1 and p.info().mma_terms == 3
+        p.set_low_accumulator(False)
+        assert p.info().low_accumulator == 0 and p.info().mma_terms == 3
+    assert binding.Plan(w, (256, 256), dtype="bf16_split", fusion_depth=1).info().low_accumulator == 0
+
+
 def _oracle_order_3d(wf, k, r1, r2, r3):
     """The 3D reading: nested staircase A' and Algorithm 1 applied level by level."""
     A = morph.crushed_weights_3d(wf, r1, r2, r3)
