@@ -246,8 +246,8 @@ sparstencil_status sparstencil_trace_read(uint64_t* out, int n);
  * copies its result out on its own stream, side by side with the others, and releases its
  * slot and bytes when its last copy completes.  A job that can never fit the budget fails
  * with SPST_ERR_NOMEM.  Plans are pooled by stencil and grid and reused by later jobs.
- * 2D jobs run the sparse tensor-core path (sparstencil_run); 3D jobs run the FP32
- * CUDA-core kernel (sparstencil_direct_run).  Results equal those of the same job run alone.
+ * 2D and 3D jobs run the sparse tensor-core path (sparstencil_run).  Results equal those of
+ * the same job run alone.
  * --------------------------------------------------------------------------------------- */
 typedef struct sparstencil_server_s* sparstencil_server_t;
 
@@ -257,9 +257,9 @@ typedef struct {
   const float* weights;      /* host cube as for sparstencil_plan, copied at submission */
   int ndim;                  /* 2 or 3 */
   const int64_t* dims;       /* copied at submission */
-  sparstencil_dtype dtype;   /* 2D jobs */
+  sparstencil_dtype dtype;
   sparstencil_boundary bc;
-  int fusion_depth;          /* 2D jobs, as for sparstencil_plan */
+  int fusion_depth;          /* as for sparstencil_plan */
   int64_t timesteps;
   const float* in_host;      /* host grid, read when the job is admitted (keep it valid until
                                 the job completes); page-locked memory lets the copies of

@@ -111,6 +111,63 @@ __global__ void __launch_bounds__(256) direct2d_kernel(const __grid_constant__ D
   }
 }
 
+// 3D, radius 1: a CTA covers 32 x 8 x 16 outputs (x, y, z); thread (x, y) keeps the 16
+// outputs of its z column in registers and adds each staged input into every output that
+// uses it.  Per output the FMAs run over the dense 3 x 3 x 3 cube in (dz, dy, dx) order,
+// zero weights included (an FMA with weight 0 leaves a finite sum unchanged, so the result
+// equals the sparse loop's over the nonzero points in the same order).
+constexpr int E3X = 32, E3Y = 8, E3Z = 16;
+
+__global__ void __launch_bounds__(256) direct3d_r1_kernel(const __grid_constant__ DirectParams p,
+                                                          const float* __restrict__ in, float* __restrict__ out) {
+  constexpr int TW = E3X + 2, TH = E3Y + 2, TD = E3Z + 2;
+  __shared__ float tile[TD * TH * TW];
+  const int64_t D = p.D, H = p.H, W = p.W;
+  const int64_t x0 = (int64_t)blockIdx.x * E3X, y0 = (int64_t)blockIdx.y * E3Y, z0 = (int64_t)blockIdx.z * E3Z;
+  for (int i = threadIdx.x; i < TW * TH * TD; i += blockDim.x) {
+    const int tz = i / (TW * TH), ty = (i / TW) % TH, tx = i % TW;
+    int64_t z = z0 + tz - 1, y = y0 + ty - 1, x = x0 + tx - 1;
+    float v = 0.f;
+    if (p.periodic) {
+      z = z < 0 ? z + D : (z >= D ? z - D : z);
+      y = y < 0 ? y + H : (y >= H ? y - H : y);
+      x = x < 0 ? x + W : (x >= W ? x - W : x);
+      v = in[(z * H + y) * W + x];
+    } else if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W) {
+      v = in[(z * H + y) * W + x];
+    }
+    tile[i] = v;
+  }
+  __syncthreads();
+  const int cx = threadIdx.x % E3X, cy = threadIdx.x / E3X;
+  float acc[E3Z];
+#pragma unroll
+  for (int k = 0; k < E3Z; k++) acc[k] = 0.f;
+  // input plane zz (tile-relative) feeds output k through weight plane dz = zz - k
+#pragma unroll
+  for (int zz = 0; zz < TD; zz++) {
+#pragma unroll
+    for (int dy = 0; dy < 3; dy++) {
+#pragma unroll
+      for (int dx = 0; dx < 3; dx++) {
+        const float v = tile[(zz * TH + cy + dy) * TW + cx + dx];
+#pragma unroll
+        for (int dz = 0; dz < 3; dz++) {
+          const int k = zz - dz;
+          if (k >= 0 && k < E3Z) acc[k] = fmaf(p.wdense[(dz * 3 + dy) * 3 + dx], v, acc[k]);
+        }
+      }
+    }
+  }
+  const int64_t y = y0 + cy, x = x0 + cx;
+  if (y < H && x < W) {
+#pragma unroll
+    for (int k = 0; k < E3Z; k++)
+      if (z0 + k < D) out[((z0 + k) * H + y) * W + x] = acc[k];
+  }
+}
+
+// 3D, radius 2-3: a CTA covers 32 x 8 x 4 outputs, FMAs over the nonzero points in order.
 constexpr int D3X = 32, D3Y = 8, D3Z = 4;
 
 __global__ void direct3d_kernel(const __grid_constant__ DirectParams p, const float* __restrict__ in,
@@ -373,6 +430,11 @@ cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* ou
       case 4: return launch_direct2d<4>(p, in, out, stream);
       default: return cudaErrorInvalidValue;
     }
+  }
+  if (r == 1) {
+    dim3 grid((unsigned)((p.W + E3X - 1) / E3X), (unsigned)((p.H + E3Y - 1) / E3Y), (unsigned)((p.D + E3Z - 1) / E3Z));
+    direct3d_r1_kernel<<<grid, 256, 0, stream>>>(p, in, out);
+    return cudaGetLastError();
   }
   dim3 grid((unsigned)((p.W + D3X - 1) / D3X), (unsigned)((p.H + D3Y - 1) / D3Y), (unsigned)((p.D + D3Z - 1) / D3Z));
   size_t smem = (size_t)(D3X + 2 * r) * (D3Y + 2 * r) * (D3Z + 2 * r) * sizeof(float);

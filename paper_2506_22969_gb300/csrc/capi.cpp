@@ -1007,7 +1007,7 @@ sparstencil_status sparstencil_direct_run(int radius, const float* weights, int 
     prm.w[prm.npts] = weights[idx];
     prm.npts++;
   }
-  if (ndim == 2)
+  if (ndim == 2 || radius == 1)
     for (int idx = 0; idx < total; idx++) prm.wdense[idx] = weights[idx];
   if (prm.H < radius || prm.W < radius || prm.D < (ndim == 3 ? radius : 1))
     return fail(SPST_ERR_UNSUPPORTED, "grid smaller than the radius");

@@ -95,7 +95,7 @@ struct DirectParams {
   int npts;
   int off[343][3];      // offsets (z, y, x) of the nonzero weights
   float w[343];         // their weights (FP32 FMAs in this order)
-  float wdense[81];     // 2D: the dense (2r+1)^2 cube (zeros included), r <= 4
+  float wdense[81];     // the dense cube (zeros included): 2D (2r+1)^2 for r <= 4, 3D 27 for r = 1
 };
 // One FP32 CUDA-core step in -> out.
 cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* out, cudaStream_t stream);

@@ -6,8 +6,8 @@
 // there: each admitted job copies its grid in, runs its sweeps and copies the result out on
 // its own stream, side by side with the others.  Plans are kept per stencil signature and
 // reused by later jobs (a plan holds device tables and a workspace, so one plan serves one
-// job at a time).  2D jobs run the sparse tensor-core path; 3D jobs, which that path does not
-// cover, run the FP32 CUDA-core kernel.  Latencies (completion minus arrival) give p50/p99.
+// job at a time).  2D and 3D jobs run the sparse tensor-core path.  Latencies (completion
+// minus arrival) give p50/p99.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -69,7 +69,7 @@ struct Job {
   int slot = -1;
   sparstencil_plan_t plan = nullptr;
   std::string key;
-  float *d_in = nullptr, *d_out = nullptr, *d_work = nullptr;
+  float *d_in = nullptr, *d_out = nullptr;
   void* d_ws = nullptr;
   size_t ws_bytes = 0;
   cudaEvent_t finished = nullptr;
@@ -121,19 +121,19 @@ struct sparstencil_server_s {
 
   // Takes the job's plan (an idle one of the same stencil and grid, else a new one: host
   // planning only) and returns the device bytes the job holds while it runs: its grids in
-  // and out plus the plan's workspace (2D) or the direct path's work grid (3D).  The planner
-  // tables kept on the device by pooled plans are small and not counted.
+  // and out plus the plan's workspace.  The planner tables kept on the device by pooled
+  // plans are small and not counted.
   size_t take_plan(Job& j, sparstencil_status* st) {
     const size_t grid = (size_t)cells(j) * sizeof(float);
     *st = SPST_OK;
-    if (j.ndim == 3) return 3 * grid;
     j.key = plan_key(j);
     auto it = idle_plans.find(j.key);
     if (it != idle_plans.end()) {
       j.plan = it->second;
       idle_plans.erase(it);
     } else {
-      *st = sparstencil_plan(j.shape, j.radius, j.weights.data(), 2, j.dims.data(), j.dtype, j.bc, j.fusion, &j.plan);
+      *st = sparstencil_plan(j.shape, j.radius, j.weights.data(), j.ndim, j.dims.data(), j.dtype, j.bc, j.fusion,
+                             &j.plan);
       if (*st != SPST_OK) return 0;
     }
     j.ws_bytes = sparstencil_workspace_bytes(j.plan);
@@ -150,27 +150,20 @@ struct sparstencil_server_s {
     const size_t grid = (size_t)cells(j) * sizeof(float);
     sparstencil_status st = SPST_OK;
     if (cudaMallocAsync((void**)&j.d_in, grid, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&j.d_out, grid, s) != cudaSuccess ||
-        (j.ndim == 3 && cudaMallocAsync((void**)&j.d_work, grid, s) != cudaSuccess))
+        cudaMallocAsync((void**)&j.d_out, grid, s) != cudaSuccess)
       st = SPST_ERR_NOMEM;
     if (st == SPST_OK && cudaMemcpyAsync(j.d_in, j.in_host, grid, cudaMemcpyHostToDevice, s) != cudaSuccess)
       st = SPST_ERR_CUDA;
     if (st == SPST_OK) {
-      if (j.ndim == 3) {
-        st = sparstencil_direct_run(j.radius, j.weights.data(), 3, j.dims.data(), j.bc, j.d_in, j.d_out, j.d_work,
-                                    j.steps, s);
-      } else {
-        // the workspace is the job's, stream-ordered like its grids, and leaves with it
-        if (cudaMallocAsync(&j.d_ws, j.ws_bytes, s) != cudaSuccess) st = SPST_ERR_NOMEM;
-        if (st == SPST_OK) st = sparstencil_bind_workspace(j.plan, j.d_ws, j.ws_bytes, s);
-        if (st == SPST_OK) st = sparstencil_run(j.plan, j.d_in, j.d_out, j.steps, s);
-      }
+      // the workspace is the job's, stream-ordered like its grids, and leaves with it
+      if (cudaMallocAsync(&j.d_ws, j.ws_bytes, s) != cudaSuccess) st = SPST_ERR_NOMEM;
+      if (st == SPST_OK) st = sparstencil_bind_workspace(j.plan, j.d_ws, j.ws_bytes, s);
+      if (st == SPST_OK) st = sparstencil_run(j.plan, j.d_in, j.d_out, j.steps, s);
     }
     if (st == SPST_OK && cudaMemcpyAsync(j.out_host, j.d_out, grid, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       st = SPST_ERR_CUDA;
     cudaFreeAsync(j.d_in, s);
     cudaFreeAsync(j.d_out, s);
-    if (j.d_work) cudaFreeAsync(j.d_work, s);
     if (j.d_ws) cudaFreeAsync(j.d_ws, s);
     if (cudaEventCreateWithFlags(&j.finished, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventRecord(j.finished, s) != cudaSuccess)

@@ -26,8 +26,8 @@ JOBS = [  # (shape, r, recipe, dims, steps, bc, dtype, t)
     ("box", 3, "gaussian", (300, 260), 9, "periodic", "bf16_split", 1),
     ("star", 1, "heat", (512, 512), 8, "dirichlet", "fp16", 1),
     ("box", 1, "random", (200, 328), 17, "dirichlet", "bf16_split", 2),
-    ("star", 1, "heat", (40, 48, 56), 6, "dirichlet", "fp32", 1),
-    ("box", 1, "random", (32, 40, 24), 5, "periodic", "fp32", 1),
+    ("star", 1, "heat", (40, 48, 56), 6, "dirichlet", "fp16_split", 1),
+    ("box", 1, "random", (32, 40, 24), 5, "periodic", "fp16", 1),
     ("box", 2, "random", (256, 256), 21, "periodic", "bf16", 3),
 ]
 
@@ -35,12 +35,8 @@ JOBS = [  # (shape, r, recipe, dims, steps, bc, dtype, t)
 def _alone(torch, w, u, shape, dims, T, bc, dtype, t):
     x = torch.from_numpy(u).cuda()
     y = torch.empty_like(x)
-    if len(dims) == 3:
-        work = torch.empty_like(x)
-        binding.direct_run(w, x, y, work, T, bc=bc)
-    else:
-        plan = binding.Plan(w, dims, dtype=dtype, bc=bc, fusion_depth=t, shape=shape)
-        plan.run(x, y, T)
+    plan = binding.Plan(w, dims, dtype=dtype, bc=bc, fusion_depth=t, shape=shape)
+    plan.run(x, y, T)
     torch.cuda.synchronize()
     return y.cpu().numpy()
 
@@ -62,8 +58,7 @@ def test_results_in_the_mix_equal_alone(torch_cuda):
             w, u = _make(k, job)
             hin = torch.from_numpy(u).pin_memory()
             hout = torch.full(dims, float("nan")).pin_memory()
-            ids.append(srv.submit(w, hin, hout, T, dtype=dtype if len(dims) == 2 else "bf16", bc=bc,
-                                  fusion_depth=t, shape=shape))
+            ids.append(srv.submit(w, hin, hout, T, dtype=dtype, bc=bc, fusion_depth=t, shape=shape))
             outs.append((k, hout))
     srv.drain()
     for jid in ids:
