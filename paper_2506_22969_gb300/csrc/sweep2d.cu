@@ -680,6 +680,11 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       soff_i[i] = (uint32_t)((n >> 3) * kSBO + (n & 7) * 16) + pairoff;
     }
     const uint32_t lut_sa = sbase + L.off_lut + 8u * (uint32_t)pl;
+    // this lane's sample of the patch constant's 8 inputs (bits of pl mod 8: 3D z, y, x;
+    // 2D row, then two bits of column)
+    const int sm = pl & 7;
+    const uint32_t c_off =
+        4u * (uint32_t)(DIM3 ? (sm >> 2) * p.box_h * P + ((sm >> 1) & 1) * P + (sm & 1) : (sm >> 2) * P + (sm & 3));
     for (int li = 0; li < ntiles_cta; li++) {
       const int stage = li & 1;
       if (!warp_wait(bar(BAR_HFULL + stage), (li >> 1) & 1, wait_ns, abort_flag, p.status)) break;
@@ -695,17 +700,15 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         // Any c gives the same sum (sum w (u - c) + c sum w); the MMAs round their FP32
         // partial sums, so c should keep |u - c| small: near the local value for smooth data
         // with an offset, near the local mean (not one sample of it) for rough zero-mean data
+        // The 16 lanes of a half-warp share the patch: lane pl loads sample pl mod 8 and an
+        // xor butterfly over 8 lanes sums them (the same sum in every lane: each level adds
+        // the same two partial sums, and FP32 addition is commutative).
         const uint32_t m0 = ba[i] + 4u * (uint32_t)(DIM3 ? (G + 1) * p.box_h * P + (G + 1) * P + G + 3
                                                          : (G + 3) * P + G + 6);
-        const uint32_t row = 4u * (uint32_t)P, plane = 4u * (uint32_t)(p.box_h * P);
-        float cs;
-        if (DIM3)
-          cs = ((lds_f32(m0) + lds_f32(m0 + 4u)) + (lds_f32(m0 + row) + lds_f32(m0 + row + 4u))) +
-               ((lds_f32(m0 + plane) + lds_f32(m0 + plane + 4u)) +
-                (lds_f32(m0 + plane + row) + lds_f32(m0 + plane + row + 4u)));
-        else
-          cs = ((lds_f32(m0) + lds_f32(m0 + 4u)) + (lds_f32(m0 + 8u) + lds_f32(m0 + 12u))) +
-               ((lds_f32(m0 + row) + lds_f32(m0 + row + 4u)) + (lds_f32(m0 + row + 8u) + lds_f32(m0 + row + 12u)));
+        float cs = lds_f32(m0 + c_off);
+        cs += __shfl_xor_sync(0xffffffffu, cs, 1);
+        cs += __shfl_xor_sync(0xffffffffu, cs, 2);
+        cs += __shfl_xor_sync(0xffffffffu, cs, 4);
         c_i[i] = 0.125f * cs;
       }
       // the patch constants go to a two-slot area of their own, so that building B'' for this
