@@ -264,6 +264,8 @@ def main():
     ap.add_argument("--suite", action="store_true", help="configs C1, C3, C4a/b (one JSON line each) and exit")
     ap.add_argument("--batch", action="store_true", help="config C4c (64 grids in one CUDA graph) and exit")
     ap.add_argument("--serve", action="store_true", help="config C5 (Poisson-arrival job server) and exit")
+    ap.add_argument("--ablation", action="store_true",
+                    help="dense versus sparse tensor-core MMAs on Box-2D49P at several sizes and exit")
     args = ap.parse_args()
     if args.suite:
         return suite_mode()
@@ -271,6 +273,8 @@ def main():
         return batch_mode()
     if args.serve:
         return serve_mode()
+    if args.ablation:
+        return ablation_mode()
     if args.impl == "reference":
         return run_reference(args)
     if args.ncu_case:
@@ -547,6 +551,47 @@ def suite_mode():
                 line[f"{dt}_rel_linf_vs_fp32_direct"] = linf
         print(json.dumps(line), flush=True)
         del x, y, work, ref_gpu
+        torch.cuda.empty_cache()
+
+
+def ablation_mode():
+    """Dense versus sparse tensor-core MMAs on the same morphed A' (the paper's breakdown of
+    CUDA cores -> dense tensor cores -> sparse tensor cores -> optimised): Box-2D49P, Gaussian
+    weights, periodic, 200 steps, BF16 single words, at several grid sizes.  One JSON line per
+    size: GStencil/s of the FP32 direct kernel, the dense and the sparse sweep at t = 1, and the
+    sparse sweep at the autotuned depth, with rel-L2 against the FP32 direct result."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_22969_gb300 import binding, inputs
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    w = inputs.stencil_weights("box", 2, 3, "gaussian", seed=4)
+    T = 200
+    for side in (1024, 2048, 4096, 8192):
+        dims = (side, side)
+        u = inputs.uniform01(4, dims)
+        x = torch.from_numpy(u).cuda()
+        y = torch.empty_like(x)
+        ref = torch.empty_like(x)
+        work = torch.empty_like(x)
+        pts = T * side * side
+        line = {"workload": f"Box-2D 49-point {side}^2, periodic, {T} steps, BF16", "points": [side, side], "steps": T}
+        ms, _ = _time_runs(lambda: binding.direct_run(w, x, ref, work, T, bc="periodic"), 2, 1, flush)
+        line["fp32_direct_gstencil_s"] = pts / ms / 1e6
+        for name, kw in (("dense_tc_t1", dict(fusion_depth=1, dense=True)), ("sparse_tc_t1", dict(fusion_depth=1)),
+                         ("sparse_tc_autotuned", dict(fusion_depth=0))):
+            try:
+                plan = binding.Plan(w, dims, dtype="bf16", bc="periodic", shape="box", **kw)
+            except binding.SparStencilError as e:
+                line[name] = f"unsupported: {e}"
+                continue
+            plan.run(x, y, T)
+            ms, _ = _time_runs(lambda: plan.run(x, y, T), 3, 1, flush)
+            line[f"{name}_gstencil_s"] = pts / ms / 1e6
+            line[f"{name}_fusion_depth"] = plan.info().fusion_depth
+            line[f"{name}_rel_l2_vs_fp32_direct"] = _rel_l2_gpu(binding, y, ref)[0]
+        print(json.dumps(line), flush=True)
+        del x, y, ref, work
         torch.cuda.empty_cache()
 
 

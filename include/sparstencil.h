@@ -75,6 +75,7 @@ typedef struct {
   int bank_conflicts;  /* residue repeats left by the planner's chunk packing (0: the B'' gather
                           reads shared memory without bank conflicts) */
   int low_accumulator; /* 1: split terms after A_hi B_hi accumulate separately (see below) */
+  int dense_ablation;  /* 1: dense tcgen05 MMAs on the uncompressed A' (see below) */
 } sparstencil_plan_info;
 
 /* Builds a plan for `shape` stencils of radius `radius` on an ndim grid of extents dims.
@@ -108,6 +109,18 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
  * SPST_ERR_UNSUPPORTED (the plan's fusion depth does not fit in TMEM this way; the plan is
  * left unchanged).  Host only. */
 sparstencil_status sparstencil_plan_set_low_accumulator(sparstencil_plan_t plan, int enable);
+
+/* The dense-versus-sparse ablation: enable != 0 runs the same morphed, permuted A' (Sec. 3.1-3.2)
+ * as dense tcgen05 MMAs (kind::f16, K = 16 per instruction, the 2:4 zeros stored explicitly in
+ * TMEM, no metadata) instead of sparse ones (Eq. 1, K = 32 per instruction).  Same tables, same
+ * gather and epilogue, same results up to the MMA summation order; it shows what the 2:4
+ * structure buys.  The uncompressed A' takes twice the TMEM columns, so a plan may fall back to
+ * one accumulator, to two BF16 split weight pieces, or (FP16 split) leave the low-order
+ * accumulator off.  The allocation-free run does not take such plans.  Must be called before the plan's first
+ * run.  Errors: SPST_ERR_INVALID (null plan, plan already ran), SPST_ERR_UNSUPPORTED (the
+ * uncompressed A' does not fit in TMEM or its staging in shared memory; the plan is left
+ * unchanged).  Host only. */
+sparstencil_status sparstencil_plan_set_dense_ablation(sparstencil_plan_t plan, int enable);
 
 /* Runs `timesteps` stencil steps: out = S^timesteps in (Sec. 2.2), on `stream`.
  *   in, out: device FP32 grids of prod(dims) elements, caller-owned, must not alias;

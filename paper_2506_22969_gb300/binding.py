@@ -37,7 +37,8 @@ class PlanInfo(ctypes.Structure):
                 ("kpad", ctypes.c_int), ("zero_columns", ctypes.c_int), ("mma_terms", ctypes.c_int),
                 ("tile_outputs", ctypes.c_int), ("num_tiles", ctypes.c_int64), ("planner_ms", ctypes.c_double),
                 ("ghost", ctypes.c_int), ("tile_pitch", ctypes.c_int), ("tile_rows", ctypes.c_int),
-                ("bank_conflicts", ctypes.c_int), ("low_accumulator", ctypes.c_int)]
+                ("bank_conflicts", ctypes.c_int), ("low_accumulator", ctypes.c_int),
+                ("dense_ablation", ctypes.c_int)]
 
 
 class Job(ctypes.Structure):
@@ -88,6 +89,7 @@ def load():
     lib.sparstencil_run_noalloc.argtypes = [vp, vp, vp, i64, vp]
     lib.sparstencil_plan_destroy.argtypes = [vp]
     lib.sparstencil_plan_set_low_accumulator.argtypes = [vp, i32]
+    lib.sparstencil_plan_set_dense_ablation.argtypes = [vp, i32]
     lib.sparstencil_workspace_bytes.argtypes = [vp]
     lib.sparstencil_workspace_bytes.restype = ctypes.c_size_t
     lib.sparstencil_bind_workspace.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -149,7 +151,7 @@ class Plan:
     """A planned stencil (sparstencil_plan); destroys itself when garbage-collected."""
 
     def __init__(self, weights, dims, dtype="bf16", bc="periodic", fusion_depth=1, shape="box",
-                 low_accumulator=None):
+                 low_accumulator=None, dense=False):
         lib = load()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
         self.ndim = w.ndim
@@ -165,6 +167,13 @@ class Plan:
         self._ws = None
         if low_accumulator is not None:  # None: the library's default for the dtype
             self.set_low_accumulator(bool(low_accumulator))
+        if dense:
+            self.set_dense_ablation(True)
+
+    def set_dense_ablation(self, enable=True):
+        """sparstencil_plan_set_dense_ablation: dense tcgen05 MMAs on the uncompressed A'
+        (before the first run)."""
+        _check(load().sparstencil_plan_set_dense_ablation(self._h, 1 if enable else 0))
 
     def set_low_accumulator(self, enable=True):
         """sparstencil_plan_set_low_accumulator: split terms after A_hi B_hi go to a TMEM

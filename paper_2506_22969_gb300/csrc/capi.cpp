@@ -76,12 +76,13 @@ struct DeviceTables {
 
 bool is_split(sparstencil_dtype d) { return d == SPST_FP16_SPLIT || d == SPST_BF16_SPLIT; }
 
-// TMEM columns: accumulators (128 each) + A'' pieces + metadata (8-column pairs of chunks).
+// TMEM columns: accumulators (128 each) + A'' pieces + metadata (8-column pairs of chunks),
+// or for the dense ablation the uncompressed A' pieces (K/2 columns each) and no metadata.
 // Returns the tile buffers that fit in the 512 columns: two accumulators when they fit, else
 // one, else 0 (does not fit); with the low-order accumulator (lo) a tile takes 256 columns
 // and there is at most one buffer.
-int tmem_accumulators(const SweepTables& T, bool lo = false) {
-  const int rest = T.a_pieces * (T.kpad / 4) + 8 * ((T.kpad / 32 + 1) / 2);
+int tmem_accumulators(const SweepTables& T, bool lo = false, bool dense = false) {
+  const int rest = dense ? T.a_pieces * (T.kpad / 2) : T.a_pieces * (T.kpad / 4) + 8 * ((T.kpad / 32 + 1) / 2);
   if (lo) return 256 + rest <= 512 ? 1 : 0;
   if (256 + rest <= 512) return 2;
   if (128 + rest <= 512) return 1;
@@ -100,6 +101,7 @@ struct sparstencil_plan_s {
   sparstencil_boundary bc;
   int requested_t = 1, t = 1, t_max = 1;
   bool lo_acc = false;  // split operands: low-order MMA terms in an accumulator of their own
+  bool dense = false;   // the dense-MMA ablation (uncompressed A', dense tcgen05 MMAs)
   bool autotune_pending = false;  // fusion_depth 0: t is chosen by timing at the first run
   std::vector<double> w64;  // input weights (FP32 values promoted exactly)
   PlanGeometry geo;
@@ -149,20 +151,23 @@ std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
   // while the weight rounding (<= 2^-17 relative per fused weight) is shared by t steps;
   // measured on the periodic Fourier closed form over 100 steps at t = 3 the rel-L2 error stays
   // below 1e-6.
-  // With the low-order accumulator a tile's two accumulators take 256 columns; three BF16
-  // pieces are kept when the rest fits beside them, else two.
+  // With the low-order accumulator a tile's two accumulators take 256 columns, and the dense
+  // ablation's uncompressed A' takes twice the columns; in every case two pieces replace three
+  // when they leave room for more tile buffers.
   const int pieces = (is_split(p->dtype) && word_of(p->dtype) == spst::Word::BF16) ? 3 : 2;
   std::string err = spst::build_sweep_tables_2d(wf, depth * p->radius, p->geo, word_of(p->dtype), pieces, true, out);
   if (!err.empty()) return err;
-  const bool retry = p->lo_acc ? tmem_accumulators(*out, true) == 0 : (depth >= 2 && tmem_accumulators(*out) < 2);
+  const int buffers3 = tmem_accumulators(*out, p->lo_acc, p->dense);
+  const bool retry = buffers3 == 0 || (!p->lo_acc && depth >= 2 && buffers3 < 2);
   if (pieces == 3 && retry) {
     SweepTables two;
     err = spst::build_sweep_tables_2d(wf, depth * p->radius, p->geo, word_of(p->dtype), 2, true, &two);
     if (!err.empty()) return err;
-    if (tmem_accumulators(two, p->lo_acc) == (p->lo_acc ? 1 : 2)) *out = std::move(two);
+    if (tmem_accumulators(two, p->lo_acc, p->dense) > tmem_accumulators(*out, p->lo_acc, p->dense))
+      *out = std::move(two);
   }
   out->t = depth;
-  if (tmem_accumulators(*out, p->lo_acc) == 0)
+  if (tmem_accumulators(*out, p->lo_acc, p->dense) == 0)
     return std::string("stencil too wide for TMEM (kpad ") + std::to_string(out->kpad) +
            (p->lo_acc ? ", with the low-order accumulator)" : ")");
   return "";
@@ -206,11 +211,13 @@ const SweepTables* tables_for(sparstencil_plan_t p, int depth, std::string* err)
 sparstencil_status ensure_device_tables(sparstencil_plan_t p, int depth, const SweepTables& T, DeviceTables** out) {
   auto& dt = p->dev_tables[depth];
   if (!dt.lut) {
+    const std::vector<uint32_t> dense_words = p->dense ? spst::dense_a_words(T, word_of(p->dtype)) : std::vector<uint32_t>();
+    const std::vector<uint32_t>& aw = p->dense ? dense_words : T.a_words;
     SPST_CUDA(cudaMalloc(&dt.lut, T.lut.size() * 4), "cudaMalloc(lut)");
-    SPST_CUDA(cudaMalloc(&dt.a_words, T.a_words.size() * 4), "cudaMalloc(a_words)");
+    SPST_CUDA(cudaMalloc(&dt.a_words, aw.size() * 4), "cudaMalloc(a_words)");
     SPST_CUDA(cudaMalloc(&dt.meta, T.meta_words.size() * 4), "cudaMalloc(meta)");
     SPST_CUDA(cudaMemcpy(dt.lut, T.lut.data(), T.lut.size() * 4, cudaMemcpyHostToDevice), "upload lut");
-    SPST_CUDA(cudaMemcpy(dt.a_words, T.a_words.data(), T.a_words.size() * 4, cudaMemcpyHostToDevice), "upload A''");
+    SPST_CUDA(cudaMemcpy(dt.a_words, aw.data(), aw.size() * 4, cudaMemcpyHostToDevice), "upload A''");
     SPST_CUDA(cudaMemcpy(dt.meta, T.meta_words.data(), T.meta_words.size() * 4, cudaMemcpyHostToDevice),
               "upload metadata");
   }
@@ -357,8 +364,9 @@ spst::Sweep2DParams sweep_params(sparstencil_plan_t p, const SweepTables& T, con
     prm.term_a[prm.nterms] = pc;
     prm.term_b[prm.nterms++] = 0;
   }
-  prm.nacc = tmem_accumulators(T, p->lo_acc);
+  prm.nacc = tmem_accumulators(T, p->lo_acc, p->dense);
   prm.lo_acc = p->lo_acc ? 1 : 0;
+  prm.dense = p->dense ? 1 : 0;
   prm.fp16 = word_of(p->dtype) == spst::Word::FP16 ? 1 : 0;
   prm.wscale = std::ldexp(1.0f, -T.wscale_log2);
   prm.lut = dt.lut;
@@ -569,6 +577,7 @@ sparstencil_status run_plan_with_buffers(sparstencil_plan_t p, const float* in, 
   if (major != 10 || minor != 3) return fail(SPST_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300)");
   const PlanGeometry& g = p->geo;
   if (g.ndim != 2) return fail(SPST_ERR_UNSUPPORTED, "the allocation-free path runs 2D plans only");
+  if (p->dense) return fail(SPST_ERR_UNSUPPORTED, "the allocation-free path runs sparse MMAs only");
   const size_t grid = ((size_t)g.Hp * (size_t)g.Wp + 63) & ~(size_t)63;  // 256-byte aligned grids
   if (2 * grid > scratch_floats)
     return fail(SPST_ERR_UNSUPPORTED, "grid too large for the allocation-free path: needs " + std::to_string(grid) +
@@ -763,6 +772,41 @@ sparstencil_status sparstencil_plan_set_low_accumulator(sparstencil_plan_t plan,
   return SPST_OK;
 }
 
+sparstencil_status sparstencil_plan_set_dense_ablation(sparstencil_plan_t plan, int enable) {
+  if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
+  if (!plan->dev_tables.empty()) return fail(SPST_ERR_INVALID, "set the MMA form before the plan's first run");
+  if ((enable != 0) == plan->dense) return SPST_OK;
+  const bool old = plan->dense, old_lo = plan->lo_acc;
+  plan->dense = enable != 0;
+  SweepTables T;
+  std::string err = build_tables(plan, plan->t, &T);
+  if (!err.empty() && plan->lo_acc) {  // the uncompressed A' leaves no room for both
+    plan->lo_acc = false;
+    err = build_tables(plan, plan->t, &T);
+  }
+  if (err.empty() && plan->dense) {
+    spst::Sweep2DParams probe;
+    std::memset(&probe, 0, sizeof(probe));
+    probe.P = plan->geo.P;
+    probe.box_h = plan->geo.box_h;
+    probe.box_d = plan->geo.box_d;
+    probe.kpad = T.kpad;
+    probe.kchunks = T.kpad / 32;
+    probe.a_pieces = T.a_pieces;
+    probe.b_pieces = is_split(plan->dtype) ? 2 : 1;
+    probe.dense = 1;
+    if (!spst::sweep2d_fits(probe)) err = "the dense A' staging does not fit in shared memory";
+  }
+  if (!err.empty()) {
+    plan->dense = old;
+    plan->lo_acc = old_lo;
+    return fail(SPST_ERR_UNSUPPORTED, err);
+  }
+  plan->full = std::move(T);
+  plan->rem.clear();
+  return SPST_OK;
+}
+
 sparstencil_status sparstencil_plan_destroy(sparstencil_plan_t plan) {
   if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
   delete plan;
@@ -942,6 +986,7 @@ sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_i
   info->tile_rows = plan->geo.box_h;
   info->bank_conflicts = plan->full.bank_conflicts;
   info->low_accumulator = plan->lo_acc ? 1 : 0;
+  info->dense_ablation = plan->dense ? 1 : 0;
   return SPST_OK;
 }
 

@@ -33,6 +33,7 @@ struct Sweep2DParams {
   int nterms;           // MMAs per K chunk; term i multiplies A piece term_a[i] by B piece term_b[i]
   int term_a[4], term_b[4];
   int nacc;             // TMEM accumulators (2: the epilogue of one tile overlaps the next tile's MMAs)
+  int dense;            // 1: the dense-MMA ablation (uncompressed A' in TMEM, dense kind::f16, K = 16)
   int lo_acc;           // split operands: 1 = the terms after the first go to a low-order accumulator
                         // (128 columns after the main one) that the epilogue adds in FP32; nacc = 1
   int nslots;           // B'' chunk slots in shared memory (1..kMaxBSlots; set by launch_sweep2d)

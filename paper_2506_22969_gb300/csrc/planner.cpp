@@ -676,6 +676,24 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   return "";
 }
 
+std::vector<uint32_t> dense_a_words(const SweepTables& T, Word word) {
+  const int M = 128, half = T.kpad / 2, dcols = T.kpad / 2;
+  std::vector<uint32_t> out((size_t)T.a_pieces * M * dcols, 0u);
+  std::vector<float> row((size_t)T.kpad);
+  for (int p = 0; p < T.a_pieces; p++)
+    for (int rho = 0; rho < M; rho++) {
+      std::fill(row.begin(), row.end(), 0.f);
+      for (int j = 0; j < half; j++) {
+        const size_t at = (size_t)rho * half + j;
+        row[(size_t)(j / 2) * 4 + T.a_idx[at]] = T.a_val[p][at];
+      }
+      for (int c = 0; c < dcols; c++)
+        out[((size_t)p * M + rho) * dcols + c] =
+            (uint32_t)to_half_bits(row[2 * c], word) | ((uint32_t)to_half_bits(row[2 * c + 1], word) << 16);
+    }
+  return out;
+}
+
 // ---------------------------------------------------------------------------------------
 // Cost model of Sec. 3.3: T = max(T_compute, T_memory), with
 //   T_compute = N_MMA * CPI / (f N_tcu)  (here: executed sparse MMA flops / tensor rate),

@@ -121,6 +121,10 @@ double layout_cost_seconds(int kt, int r1, int r2, int64_t H, int64_t W, int kpa
 // Round-to-nearest-even conversions (host side) of an FP32 value to FP16 / BF16, returned
 // as the 16-bit pattern and as the exact value in FP32.
 uint16_t to_half_bits(float x, Word word);
+// TMEM image of the uncompressed permuted A' (the dense-MMA ablation): [a_pieces][M][kpad/2]
+// words, column j of lane rho holding K elements 2j (low half) and 2j+1; the 2:4 zeros are
+// stored explicitly.
+std::vector<uint32_t> dense_a_words(const SweepTables& T, Word word);
 float half_bits_to_float(uint16_t h, Word word);
 
 }  // namespace spst

@@ -200,6 +200,16 @@ __device__ __forceinline__ void issue_chunk(int nterms, uint32_t d, uint32_t d1,
 #undef SPST_PREDS
 }
 
+// One dense MMA (kind::f16, M = 128, N = 128, K = 16; A in TMEM, B from a shared-memory
+// descriptor) by one elected lane of a converged warp; acc = 0 overwrites the accumulator.
+__device__ __forceinline__ void mma_dense_elected(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred e, q;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 q, %4, 0;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, q;\n}" ::"r"(d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ uint32_t pack2(float lo, float hi, int fp16) {
   uint32_t r;
   if (fp16)
@@ -316,7 +326,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   volatile int* abort_flag = (volatile int*)(smem + L.off_bar + 272);
   int32_t* lut_s = (int32_t*)(smem + L.off_lut);
   const int pieces = p.a_pieces;
-  const int acols = p.kpad / 4;
+  const int acols = p.dense ? p.kpad / 2 : p.kpad / 4;  // TMEM columns per A piece
   const int nacc = p.nacc;
   const uint64_t wait_ns = p.wait_ns;
 
@@ -366,8 +376,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                    : "memory");
     }
-    for (int i = threadIdx.x; i < 128 * p.kchunks; i += blockDim.x)
-      sts_u32(stage_m + 4u * (uint32_t)((i / p.kchunks) * mpitch + i % p.kchunks), p.meta_words[i]);
+    if (!p.dense)
+      for (int i = threadIdx.x; i < 128 * p.kchunks; i += blockDim.x)
+        sts_u32(stage_m + 4u * (uint32_t)((i / p.kchunks) * mpitch + i % p.kchunks), p.meta_words[i]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -399,8 +410,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       }
     }
     // chunk c's metadata column: an 8-column-aligned pair per two chunks, the instruction's
-    // sparsity selector (0/1) picks the column inside the pair
-    for (int c = 0; c < p.kchunks; c++) {
+    // sparsity selector (0/1) picks the column inside the pair (none for the dense ablation)
+    for (int c = 0; c < (p.dense ? 0 : p.kchunks); c++) {
       uint32_t v;
       asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(stage_m + 4u * (uint32_t)(row * mpitch + c)));
       asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(
@@ -481,6 +492,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     idesc |= (p.fp16 ? 0u : 1u) << 10;     // B: FP16 (0) / BF16 (1)
     idesc |= (uint32_t)(128 >> 3) << 17;   // N = 128
     idesc |= (uint32_t)(128 >> 4) << 24;   // M = 128
+    const uint32_t idesc_dense = idesc & ~(1u << 2);  // the same shape and types, dense
     const int nterms = p.nterms;
     uint32_t a_term[4], b_term[4];  // TMEM address of the term's A'' piece; B piece offset (16-byte units)
 #pragma unroll
@@ -522,8 +534,26 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         const uint64_t b1 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[1]);
         const uint64_t b2 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[2]);
         const uint64_t b3 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[3]);
-        issue_chunk(nterms, dcol, dcol1, a_term[0] + a8, a_term[1] + a8, a_term[2] + a8, a_term[3] + a8, b0, b1, b2, b3,
-                    meta, idesc_kc, kc > 0 ? 1u : 0u, (kc > 0 || !p.lo_acc) ? 1u : 0u, bar(BAR_BEMPTY + slot));
+        if (p.dense) {
+          // dense ablation: two K = 16 MMAs per term and chunk (A columns 16kc and 16kc + 8,
+          // B rows 0-15 and 16-31 of the chunk: two core matrices of 16 bytes along K = 2 LBO)
+          const uint64_t bt[4] = {b0, b1, b2, b3};
+#pragma unroll
+          for (int t = 0; t < 4; t++) {
+            if (t < nterms) {
+#pragma unroll
+              for (int h = 0; h < 2; h++) {
+                const uint32_t acc = (h > 0 || kc > 0) ? 1u : (t == 0 ? 0u : (t == 1 && p.lo_acc ? 0u : 1u));
+                mma_dense_elected(t == 0 ? dcol : dcol1, a_term[t] + 16u * (uint32_t)kc + 8u * (uint32_t)h,
+                                  bt[t] + (uint64_t)(h * (2 * kLBO >> 4)), idesc_dense, acc);
+              }
+            }
+          }
+          commit_elected(bar(BAR_BEMPTY + slot));
+        } else {
+          issue_chunk(nterms, dcol, dcol1, a_term[0] + a8, a_term[1] + a8, a_term[2] + a8, a_term[3] + a8, b0, b1, b2,
+                      b3, meta, idesc_kc, kc > 0 ? 1u : 0u, (kc > 0 || !p.lo_acc) ? 1u : 0u, bar(BAR_BEMPTY + slot));
+        }
         trace_chunk(tr && li == 1 && lane == 0, 2, kc, 1);
       }
       if (!ok) break;
@@ -838,8 +868,8 @@ cudaError_t sweep_trace_read(unsigned long long* out, int n) {
 #endif
 // Bytes of the A'' / metadata staging area used during set-up.
 static size_t staging_bytes(const Sweep2DParams& p) {
-  const int acols = p.kpad / 4;
-  return 4u * ((size_t)p.a_pieces * 128 * (acols + 4) + (size_t)128 * (p.kchunks | 1));
+  const int acols = p.dense ? p.kpad / 2 : p.kpad / 4;
+  return 4u * ((size_t)p.a_pieces * 128 * (acols + 4) + (p.dense ? 0 : (size_t)128 * (p.kchunks | 1)));
 }
 
 int sweep2d_max_slots(const Sweep2DParams& p) {

@@ -24,9 +24,9 @@ def torch_cuda():
     return torch
 
 
-def _run_sparse(torch, u, w, steps, dtype, bc, t, shape, low_accumulator=None):
+def _run_sparse(torch, u, w, steps, dtype, bc, t, shape, low_accumulator=None, dense=False):
     plan = binding.Plan(w, u.shape, dtype=dtype, bc=bc, fusion_depth=t, shape=shape,
-                        low_accumulator=low_accumulator)
+                        low_accumulator=low_accumulator, dense=dense)
     x = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).cuda()
     y = torch.empty_like(x)
     plan.run(x, y, steps)
@@ -54,6 +54,7 @@ CASES = [
     ("box", 1, "random", (130, 200), 10, "dirichlet", "bf16_split", 4),
     ("box", 2, "gaussian", (300, 260), 7, "dirichlet", "bf16_split", 2),
     ("star", 3, "gaussian", (260, 300), 9, "dirichlet", "bf16", 2),
+    ("box", 3, "gaussian", (260, 300), 8, "periodic", "bf16_split", 2),
 ]
 
 
@@ -329,3 +330,24 @@ def test_low_accumulator_matches_oracle(torch_cuda, oracle_mod, ndim, shape, dim
     assert np.all(np.isfinite(two))
     assert l2_two <= TOL[dtype], (l2_two, linf_two)
     assert l2_two <= 1.05 * l2_one, (l2_two, l2_one)
+
+
+@pytest.mark.parametrize("ndim,shape,r,recipe,dims,steps,bc,dtype,t", [
+    (2, "box", 1, "random", (300, 260), 12, "periodic", "bf16", 1),
+    (2, "box", 1, "random", (260, 300), 9, "periodic", "bf16_split", 3),
+    (2, "star", 3, "gaussian", (256, 384), 6, "dirichlet", "bf16", 1),
+    (2, "box", 3, "gaussian", (256, 256), 4, "periodic", "bf16", 1),
+    (3, "box", 1, "random", (32, 36, 128), 8, "periodic", "fp16_split", 1),
+    (3, "star", 1, "random", (20, 40, 70), 5, "dirichlet", "fp16", 1),
+])
+def test_dense_ablation_matches_oracle(torch_cuda, oracle_mod, ndim, shape, r, recipe, dims, steps, bc, dtype, t):
+    """The dense-MMA ablation (uncompressed A', dense kind::f16 MMAs) computes the same
+    stencil: within the dtype's tolerance of the oracle, like the sparse path."""
+    w = inputs.stencil_weights(shape, ndim, r, recipe, seed=14)
+    u = inputs.uniform01(8, dims)
+    ref = oracle_mod.run(u, w, bc, steps)
+    got, plan = _run_sparse(torch_cuda, u, w, steps, dtype, bc, t, shape, dense=True)
+    assert plan.info().dense_ablation == 1
+    l2, linf = oracle_mod.rel_errors(got, ref)
+    assert np.all(np.isfinite(got))
+    assert l2 <= TOL[dtype], (l2, linf)

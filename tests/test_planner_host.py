@@ -240,9 +240,11 @@ def test_autotune_plan_takes_the_deepest_depth_that_fits(lib):
     w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
     p = binding.Plan(w, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=0)
     assert p.info().fusion_depth == 3 and p.info().ghost == 3
+    # 7x7 box, split: t = 3 (K_pad 960) does not fit TMEM; t = 2 (K_pad 576) fits with two
+    # BF16 weight pieces beside one accumulator
     w3 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=2)
     p3 = binding.Plan(w3, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=0)
-    assert p3.info().fusion_depth == 1
+    assert p3.info().fusion_depth == 2 and p3.info().mma_terms == 3
 
 
 def test_low_accumulator_setting(lib):
@@ -264,7 +266,7 @@ def test_low_accumulator_setting(lib):
     assert p3.info().low_accumulator == 1 and p3.info().mma_terms == 3
     p3.set_low_accumulator(False)
     assert p3.info().low_accumulator == 0
-    # a 7x7 box at t = 1 (K 480 after padding) leaves no room for the second accumulator
+    # a 7x7 box at t = 1 (K_pad 320): checked against the TMEM budget of the second accumulator
     w7 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=2)
     p7 = binding.Plan(w7, (512, 512), dtype="fp16_split", fusion_depth=1)
     kpad = p7.info().kpad
@@ -281,6 +283,33 @@ def test_low_accumulator_setting(lib):
         p.set_low_accumulator(False)
         assert p.info().low_accumulator == 0 and p.info().mma_terms == 3
     assert binding.Plan(w, (256, 256), dtype="bf16_split", fusion_depth=1).info().low_accumulator == 0
+
+
+def test_dense_ablation_setting(lib):
+    """The dense-MMA ablation: set before the first run; the uncompressed A' takes K/2 TMEM
+    columns per piece, and a plan whose A' does not fit is refused and left as it was."""
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
+    p = binding.Plan(w, (256, 256), dtype="bf16_split", fusion_depth=1)
+    info = p.info()
+    p.set_dense_ablation(True)
+    assert p.info().dense_ablation == 1 and p.info().kpad == info.kpad
+    p.set_dense_ablation(False)
+    assert p.info().dense_ablation == 0
+    # FP16 split 3D: the low-order accumulator gives way to the uncompressed A'
+    w3 = inputs.stencil_weights("box", 3, 1, "random", seed=3)
+    p3 = binding.Plan(w3, (32, 32, 128), dtype="fp16_split", fusion_depth=1, shape="box")
+    assert p3.info().low_accumulator == 1
+    p3.set_dense_ablation(True)
+    assert p3.info().dense_ablation == 1 and p3.info().low_accumulator == 0
+    # a 7x7 box at t = 2 (K_pad 576): two uncompressed pieces of 288 columns do not fit
+    w7 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=2)
+    p7 = binding.Plan(w7, (512, 512), dtype="bf16", fusion_depth=2)
+    with pytest.raises(binding.SparStencilError) as e:
+        p7.set_dense_ablation(True)
+    assert e.value.code == 2 and p7.info().dense_ablation == 0
+    # at t = 1 (K_pad 320) split operands fit with two pieces (three would not)
+    p71 = binding.Plan(w7, (512, 512), dtype="bf16_split", fusion_depth=1, dense=True)
+    assert p71.info().dense_ablation == 1 and p71.info().mma_terms == 3
 
 
 def _oracle_order_3d(wf, k, r1, r2, r3):
