@@ -76,6 +76,9 @@ typedef struct {
                           reads shared memory without bank conflicts) */
   int low_accumulator; /* 1: split terms after A_hi B_hi accumulate separately (see below) */
   int dense_ablation;  /* 1: dense tcgen05 MMAs on the uncompressed A' (see below) */
+  int pairing;         /* column pairs of the 2:4 conversion: 0 = Algorithm 1 (Sec. 3.2), 1 = a
+                          maximum matching on the stencil's actual support, taken when the
+                          support is smaller than the box and that needs fewer K chunks */
 } sparstencil_plan_info;
 
 /* Builds a plan for `shape` stencils of radius `radius` on an ndim grid of extents dims.

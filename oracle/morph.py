@@ -164,6 +164,26 @@ def min_zero_columns_bruteforce(E: np.ndarray) -> int:
     return n - 2 * best((1 << n) - 1)
 
 
+def max_matching_pairs(A: np.ndarray):
+    """Problem 1 on the actual support of A (the maximum-matching pairing used when a stencil's
+    support is smaller than the box): the nonzero columns of A, two of them compatible when no
+    row has both nonzero (Def. 1), paired by a maximum-cardinality matching (networkx's
+    implementation of Edmonds' algorithm, a library primitive); every unmatched nonzero column
+    gets a zero partner.  Returns (pairs, zero columns); all-zero columns of A take no part."""
+    import networkx as nx
+    nz = np.where(np.any(A != 0, axis=0))[0]
+    S = (A[:, nz] != 0).astype(np.int64)
+    G = nx.Graph()
+    G.add_nodes_from(range(len(nz)))
+    ii, jj = np.where(np.triu((S.T @ S) == 0, 1))
+    G.add_edges_from(zip(ii.tolist(), jj.tolist()))
+    M = nx.max_weight_matching(G, maxcardinality=True)
+    pairs = [(int(nz[a]), int(nz[b])) for a, b in M]
+    matched = {v for a, b in M for v in (a, b)}
+    pairs += [(int(nz[i]), ZERO) for i in range(len(nz)) if i not in matched]
+    return pairs, len(nz) - 2 * len(M)
+
+
 def hierarchical_matching(n: int, g: int, k: int):
     """Algorithm 1 (hierarchical two-level matching), literally.
 

@@ -38,7 +38,7 @@ class PlanInfo(ctypes.Structure):
                 ("tile_outputs", ctypes.c_int), ("num_tiles", ctypes.c_int64), ("planner_ms", ctypes.c_double),
                 ("ghost", ctypes.c_int), ("tile_pitch", ctypes.c_int), ("tile_rows", ctypes.c_int),
                 ("bank_conflicts", ctypes.c_int), ("low_accumulator", ctypes.c_int),
-                ("dense_ablation", ctypes.c_int)]
+                ("dense_ablation", ctypes.c_int), ("pairing", ctypes.c_int)]
 
 
 class Job(ctypes.Structure):

@@ -987,6 +987,7 @@ sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_i
   info->bank_conflicts = plan->full.bank_conflicts;
   info->low_accumulator = plan->lo_acc ? 1 : 0;
   info->dense_ablation = plan->dense ? 1 : 0;
+  info->pairing = plan->full.pairing;
   return SPST_OK;
 }
 

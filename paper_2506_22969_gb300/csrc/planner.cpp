@@ -170,6 +170,95 @@ std::vector<std::pair<int, int>> hierarchical_matching_nd(const std::vector<int>
 }
 
 // ---------------------------------------------------------------------------------------
+// Maximum-cardinality matching in a general graph (Edmonds' blossom algorithm, 1965): from
+// each free vertex grow an alternating tree by breadth-first search; an edge that closes an
+// odd cycle (a blossom) contracts the cycle onto its base, whose vertices all become outer
+// vertices of the tree; reaching a free vertex gives an augmenting path, which is flipped.
+// A greedy pass seeds the matching.  Returns mate[v] (-1: unmatched).
+// ---------------------------------------------------------------------------------------
+std::vector<int> max_cardinality_matching(const std::vector<std::vector<int>>& adj) {
+  const int n = (int)adj.size();
+  std::vector<int> mate(n, -1), parent(n, -1), base(n), queue(n);
+  std::vector<char> outer(n, 0), in_blossom(n, 0), seen(n, 0);
+  // the first common base of a and b on their paths to the root
+  auto common_base = [&](int a, int b) {
+    std::fill(seen.begin(), seen.end(), 0);
+    for (;;) {
+      a = base[a];
+      seen[a] = 1;
+      if (mate[a] < 0) break;
+      a = parent[mate[a]];
+    }
+    for (;;) {
+      b = base[b];
+      if (seen[b]) return b;
+      b = parent[mate[b]];
+    }
+  };
+  // marks the blossom vertices on the path from v down to base b, re-pointing parents
+  auto mark = [&](int v, int b, int child) {
+    while (base[v] != b) {
+      in_blossom[base[v]] = in_blossom[base[mate[v]]] = 1;
+      parent[v] = child;
+      child = mate[v];
+      v = parent[mate[v]];
+    }
+  };
+  auto augmenting_end = [&](int root) -> int {
+    std::fill(outer.begin(), outer.end(), 0);
+    std::fill(parent.begin(), parent.end(), -1);
+    for (int i = 0; i < n; i++) base[i] = i;
+    int head = 0, tail = 0;
+    outer[root] = 1;
+    queue[tail++] = root;
+    while (head < tail) {
+      const int v = queue[head++];
+      for (int to : adj[v]) {
+        if (base[v] == base[to] || mate[v] == to) continue;
+        if (to == root || (mate[to] >= 0 && parent[mate[to]] >= 0)) {
+          const int b = common_base(v, to);
+          std::fill(in_blossom.begin(), in_blossom.end(), 0);
+          mark(v, b, to);
+          mark(to, b, v);
+          for (int i = 0; i < n; i++)
+            if (in_blossom[base[i]]) {
+              base[i] = b;
+              if (!outer[i]) {
+                outer[i] = 1;
+                queue[tail++] = i;
+              }
+            }
+        } else if (parent[to] < 0) {
+          parent[to] = v;
+          if (mate[to] < 0) return to;
+          outer[mate[to]] = 1;
+          queue[tail++] = mate[to];
+        }
+      }
+    }
+    return -1;
+  };
+  for (int v = 0; v < n; v++)
+    if (mate[v] < 0)
+      for (int to : adj[v])
+        if (mate[to] < 0) {
+          mate[v] = to;
+          mate[to] = v;
+          break;
+        }
+  for (int v = 0; v < n; v++) {
+    if (mate[v] >= 0) continue;
+    for (int u = augmenting_end(v); u >= 0;) {
+      const int pv = parent[u], next = mate[pv];
+      mate[u] = pv;
+      mate[pv] = u;
+      u = next;
+    }
+  }
+  return mate;
+}
+
+// ---------------------------------------------------------------------------------------
 // Packing matched pairs into K chunks of `slots` (16) pairs so that, within every chunk,
 // the first-column offsets and the second-column offsets are distinct mod 16 (see the
 // gather's bank rule in build_sweep_tables_2d).  View each pair as an edge between its
@@ -535,6 +624,49 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
       continue;
     }
     kept.push_back(pr);
+  }
+  // A support smaller than the box (stars, custom masks) leaves A' columns that are zero, and
+  // Algorithm 1's block pairing, built for the full staircase, may then pad more than needed.
+  // Problem 1 on the actual support is a maximum matching in the graph of nonzero columns
+  // whose row supports are disjoint (such a pair holds at most one nonzero per row); it is
+  // taken when it needs fewer 32-row K chunks.
+  std::vector<int> nzcols;
+  for (int kap = 0; kap < kp; kap++)
+    if (colnz[kap]) nzcols.push_back(kap);
+  if (drop_zero_pairs && (int)nzcols.size() < kp) {
+    const int n = (int)nzcols.size();
+    std::vector<std::vector<uint64_t>> rows(n, std::vector<uint64_t>((size_t)(M + 63) / 64, 0));
+    for (int i = 0; i < n; i++)
+      for (int rho = 0; rho < M; rho++)
+        if (aval(rho, nzcols[i]) != 0.f) rows[i][rho / 64] |= 1ull << (rho % 64);
+    std::vector<std::vector<int>> adj(n);
+    for (int i = 0; i < n; i++)
+      for (int j = i + 1; j < n; j++) {
+        bool disjoint = true;
+        for (size_t wd = 0; wd < rows[i].size() && disjoint; wd++) disjoint = (rows[i][wd] & rows[j][wd]) == 0;
+        if (disjoint) {
+          adj[i].push_back(j);
+          adj[j].push_back(i);
+        }
+      }
+    const std::vector<int> mate = max_cardinality_matching(adj);
+    std::vector<std::pair<int, int>> mpairs;
+    int unmatched = 0;
+    for (int i = 0; i < n; i++) {
+      if (mate[i] < 0) {
+        mpairs.push_back({nzcols[i], -1});
+        unmatched++;
+      } else if (i < mate[i]) {
+        mpairs.push_back({nzcols[i], nzcols[mate[i]]});
+      }
+    }
+    const int chunk_pairs = Tile2D::KCHUNK / 2;
+    if ((mpairs.size() + chunk_pairs - 1) / chunk_pairs < (kept.size() + chunk_pairs - 1) / chunk_pairs) {
+      kept = std::move(mpairs);
+      T.zero_cols = unmatched;
+      T.dropped_pairs = 0;
+      T.pairing = 1;
+    }
   }
   // Lookup-table offsets (Sec. 3.3): tile word of column (u, c) relative to the patch base
   // (py*R2*P + px*R1).  The tile starts G cells before the tile's first output, the patch

@@ -52,6 +52,7 @@ struct SweepTables {
   int zero_cols = 0;       // zero nodes inserted by Algorithm 1
   int dropped_pairs = 0;   // matched pairs whose two columns are both all-zero (removed)
   int bank_conflicts = 0;  // repeated residues left by the chunk packing (0: conflict-free gather)
+  int pairing = 0;         // 0: Algorithm 1's pairs; 1: maximum matching on the actual support
   std::vector<double> wfused;     // (2R+1)^ndim composed weights (FP64)
   std::vector<float> wfused32;    // the same rounded to FP32 (the values the pieces split)
   std::vector<int> order;         // kpad: original A' column per permuted position, -1 = zero column
@@ -125,6 +126,9 @@ uint16_t to_half_bits(float x, Word word);
 // words, column j of lane rho holding K elements 2j (low half) and 2j+1; the 2:4 zeros are
 // stored explicitly.
 std::vector<uint32_t> dense_a_words(const SweepTables& T, Word word);
+// Maximum-cardinality matching of a general graph given by adjacency lists (Edmonds' blossom
+// algorithm); returns each vertex's mate, -1 for unmatched vertices.
+std::vector<int> max_cardinality_matching(const std::vector<std::vector<int>>& adj);
 float half_bits_to_float(uint16_t h, Word word);
 
 }  // namespace spst

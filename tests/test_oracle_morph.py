@@ -139,6 +139,39 @@ def test_theorem2_validity_and_minimality(k, r1, r2, alg1, brute):
     assert morph.min_zero_columns_bruteforce(E) == brute
 
 
+@pytest.mark.parametrize("mask,r1,r2", [
+    ("box3", 1, 1), ("box3", 3, 2), ("box3", 5, 1), ("box3", 1, 5), ("star3", 2, 2), ("star3", 4, 1),
+    ("star5", 1, 1), ("star5", 2, 1), ("cross3", 2, 2)])
+def test_max_matching_pairing_is_minimal(mask, r1, r2):
+    """The maximum-matching pairing (Problem 1 on the actual support) is valid (Def. 3) and
+    reaches the brute-force optimum; for box masks where Algorithm 1 pads more (r1 = 5) it
+    pads less."""
+    pytest.importorskip("networkx")
+    k = int(mask[-1])
+    w = np.ones((k, k))
+    if mask.startswith("star"):
+        w = np.zeros((k, k))
+        w[k // 2, :] = 1.0
+        w[:, k // 2] = 1.0
+    elif mask.startswith("cross"):  # an asymmetric support: centre, right and lower neighbour
+        w = np.zeros((k, k))
+        w[1, 1] = w[1, 2] = w[2, 1] = 1.0
+    A = morph.crushed_weights(w, r1, r2)
+    E = morph.conflict_graph(A)
+    pairs, zeros = morph.max_matching_pairs(A)
+    nz = np.any(A != 0, axis=0)
+    # restricted to the nonzero columns the pairing covers each exactly once, without conflicts
+    cols = [v for pr in pairs for v in pr if v != ZERO]
+    assert sorted(cols) == sorted(np.where(nz)[0].tolist())
+    assert all(b == ZERO or not E[a, b] for a, b in pairs)
+    assert zeros == sum(1 for a, b in pairs if b == ZERO)
+    sub = E[np.ix_(nz, nz)]
+    assert zeros == morph.min_zero_columns_bruteforce(sub)
+    if mask == "box3" and (r1, r2) in ((5, 1), (1, 5)):
+        _, _, M = morph.hierarchical_matching(A.shape[1], k + r1 - 1, k)
+        assert zeros < sum(1 for a, b in M if b == ZERO)
+
+
 @pytest.mark.parametrize("shape,k,r1,r2", [("box", 3, 16, 8), ("box", 5, 16, 8), ("box", 7, 16, 8),
                                            ("star", 7, 16, 8), ("box", 3, 8, 16), ("box", 5, 4, 3)])
 def test_pit_2_4_and_invariance(shape, k, r1, r2):
