@@ -45,6 +45,14 @@ METRIC = "GStencil/s per GB300, sparse-TCU vs plain FP32 at stated L2 err; p99 l
 FALLBACK_HBM_GBS = 6800.0
 
 
+def _peak_bf16_tflops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -325,13 +333,20 @@ def main():
     candidates = [args.fusion] if args.fusion > 0 else [1, 2, 3]
     tune = {}
 
+    # the Sec. 3.3 cost model beside the measured search: sparse tensor rate = 2 x the measured
+    # dense BF16 rate, HBM = the measured copy bandwidth, shared memory = 128 B per clock per SM
+    model_rates = (2.0 * _peak_bf16_tflops() * 1e12, _peaks()[0] * 1e9, 128.0 * 152 * 1.9e9)
+    model = {}
+
     def autotune(dtype):
         best = None
         tune[dtype] = {}
+        model[dtype] = {}
         for t in candidates:
             pl = binding.Plan(w, (H, W), dtype=dtype, bc=cfg["bc"], fusion_depth=t, shape=cfg["shape"])
             ms = min(timed_runs(lambda: pl.run(x, y, T), 2, 1))
             tune[dtype][str(t)] = ms
+            model[dtype][str(t)] = pl.cost_model(t, *model_rates) * T * 1e3
             if best is None or ms < best[1]:
                 best = (t, ms, pl)
         return best
@@ -443,6 +458,9 @@ def main():
             "clocks": clock_info,
             "variants": variants,
             "autotune_ms_per_run": tune,
+            "cost_model_ms_per_run": model,
+            "cost_model_picks_measured_best": {
+                d: min(model[d], key=model[d].get) == min(tune[d], key=tune[d].get) for d in tune},
             "rel_l2_sampled": rel_split,
             "device_status": status,
             "planner_ms": info.planner_ms,

@@ -190,6 +190,18 @@ sparstencil_status sparstencil_bind_workspace(sparstencil_plan_t plan, void* dev
 sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const float* const* in,
                                          float* const* out, const int64_t* steps, int n, cudaStream_t stream);
 
+/* The cost model of Sec. 3.3 (Eq. 6-11), T = max(T_compute, T_memory), for a sweep of depth
+ * `depth` (1 .. the plan's fusion depth) of this plan, written to *seconds_per_step as the
+ * sweep's time divided by depth.  T_compute = executed sparse MMA flops / tensor_flops (one
+ * 128x128x32 MMA per K chunk, 128-patch tile and MMA term); T_memory = max(8 B per output /
+ * hbm_bytes_per_s, (data_transR + data_transW) / smem_bytes_per_s) with data_trans =
+ * k'(m'/2 + n') 16-bit elements per operand piece (reading: m means m').  The rates are the
+ * caller's (measured or nominal).  Host only; builds the depth's tables if needed.
+ * Errors: SPST_ERR_INVALID (null pointers, depth out of range, rates not positive). */
+sparstencil_status sparstencil_cost_model(sparstencil_plan_t plan, int depth, double tensor_flops,
+                                          double hbm_bytes_per_s, double smem_bytes_per_s,
+                                          double* seconds_per_step);
+
 /* Fills *info (host only). */
 sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_info* info);
 

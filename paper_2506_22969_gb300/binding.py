@@ -90,6 +90,8 @@ def load():
     lib.sparstencil_plan_destroy.argtypes = [vp]
     lib.sparstencil_plan_set_low_accumulator.argtypes = [vp, i32]
     lib.sparstencil_plan_set_dense_ablation.argtypes = [vp, i32]
+    lib.sparstencil_cost_model.argtypes = [vp, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_double)]
     lib.sparstencil_workspace_bytes.argtypes = [vp]
     lib.sparstencil_workspace_bytes.restype = ctypes.c_size_t
     lib.sparstencil_bind_workspace.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -169,6 +171,13 @@ class Plan:
             self.set_low_accumulator(bool(low_accumulator))
         if dense:
             self.set_dense_ablation(True)
+
+    def cost_model(self, depth, tensor_flops, hbm_bytes_per_s, smem_bytes_per_s) -> float:
+        """sparstencil_cost_model: the Sec. 3.3 model's seconds per time step at this depth."""
+        out = ctypes.c_double()
+        _check(load().sparstencil_cost_model(self._h, int(depth), float(tensor_flops), float(hbm_bytes_per_s),
+                                             float(smem_bytes_per_s), ctypes.byref(out)))
+        return out.value
 
     def set_dense_ablation(self, enable=True):
         """sparstencil_plan_set_dense_ablation: dense tcgen05 MMAs on the uncompressed A'

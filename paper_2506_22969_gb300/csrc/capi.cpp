@@ -991,6 +991,30 @@ sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_i
   return SPST_OK;
 }
 
+sparstencil_status sparstencil_cost_model(sparstencil_plan_t plan, int depth, double tensor_flops, double hbm_bytes_per_s,
+                                          double smem_bytes_per_s, double* seconds_per_step) {
+  if (!plan || !seconds_per_step) return fail(SPST_ERR_INVALID, "null argument");
+  if (depth < 1 || depth > plan->t_max) return fail(SPST_ERR_INVALID, "depth must be in 1..the plan's fusion depth");
+  if (!(tensor_flops > 0) || !(hbm_bytes_per_s > 0) || !(smem_bytes_per_s > 0))
+    return fail(SPST_ERR_INVALID, "rates must be positive");
+  std::string err;
+  const SweepTables* T = depth == plan->t ? &plan->full : tables_for(plan, depth, &err);
+  if (!T) return fail(SPST_ERR_UNSUPPORTED, err);
+  // Eq. 6-11 with the plan's layout: m' = 128 rows, k' = A' columns, n' = outputs / m'
+  // patches; one MMA per 32-row K chunk, 128-patch tile and MMA term; data_R + data_W = 8 B
+  // per output; data_transR = data_transW = k' (m'/2 + n') 16-bit elements per operand piece.
+  const double cells = (double)plan->cells();
+  const double mprime = 128.0, kprime = (double)T->kprime, nprime = cells / mprime;
+  const int terms = (is_split(plan->dtype) ? 2 : 1) + T->a_pieces - 1;
+  const double n_mma = (double)(T->kpad / 32) * std::ceil(nprime / 128.0) * terms;
+  const double t_compute = n_mma * 2.0 * 128.0 * 128.0 * 32.0 / tensor_flops;
+  const double data_rw = 8.0 * cells;
+  const double trans = kprime * (mprime / 2.0 + nprime) * 2.0 * (is_split(plan->dtype) ? 2 : 1);
+  const double t_memory = std::max(data_rw / hbm_bytes_per_s, 2.0 * trans / smem_bytes_per_s);
+  *seconds_per_step = std::max(t_compute, t_memory) / depth;
+  return SPST_OK;
+}
+
 sparstencil_status sparstencil_table_kpad(sparstencil_plan_t plan, int which, int remainder_depth, int* kpad) {
   if (!plan || !kpad) return fail(SPST_ERR_INVALID, "null argument");
   std::string err;

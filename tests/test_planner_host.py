@@ -328,6 +328,27 @@ def test_dense_ablation_setting(lib):
     assert p71.info().dense_ablation == 1 and p71.info().mma_terms == 3
 
 
+def test_cost_model_entry_point(lib):
+    """sparstencil_cost_model (Eq. 6-11): with a fast tensor pipe the HBM term binds and the
+    time per step falls as 1/t; with a slow one the compute term binds and grows with the
+    executed MMAs (K chunks x terms); bad arguments are refused."""
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
+    p = binding.Plan(w, (4096, 4096), dtype="bf16_split", fusion_depth=3)
+    fast = (1e18, 6790e9, 1e18)
+    per_step = [p.cost_model(t, *fast) for t in (1, 2, 3)]
+    hbm = 8.0 * 4096 * 4096 / 6790e9
+    np.testing.assert_allclose(per_step, [hbm, hbm / 2, hbm / 3], rtol=1e-12)
+    slow = (1e12, 1e18, 1e18)
+    t3 = p.cost_model(3, *slow)
+    info = p.info()
+    n_mma = (info.kpad // 32) * (4096 * 4096 // 128 // 128) * info.mma_terms
+    assert t3 == pytest.approx(n_mma * 2 * 128 * 128 * 32 / 1e12 / 3, rel=1e-12)
+    for bad in ((0, *fast), (4, *fast), (1, 0.0, 1e9, 1e9)):
+        with pytest.raises(binding.SparStencilError) as e:
+            p.cost_model(*bad)
+        assert e.value.code == 1
+
+
 def _oracle_order_3d(wf, k, r1, r2, r3):
     """The 3D reading: nested staircase A' and Algorithm 1 applied level by level."""
     A = morph.crushed_weights_3d(wf, r1, r2, r3)
