@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -505,61 +506,70 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     const uint64_t desc0 = make_sdesc(sbase + L.off_b, kLBO, kSBO);
     const uint32_t dlo0 = (uint32_t)desc0, dhi = (uint32_t)(desc0 >> 32);
     const uint32_t slot_step = L.slot_bytes >> 4;
-    uint32_t mslot = 0, mphase = 0;  // chunk ring position and wrap parity
-    bool ok = true;
-    for (int li = 0; li < ntiles_cta && ok; li++) {
-      const int acc = li % nacc, use = li / nacc;
-      if (use > 0 && !warp_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      trace(tr && lane == 0, 1, li, 0);
-      const uint32_t dcol = tmem + (uint32_t)acc * acc_stride;
-      const uint32_t dcol1 = p.lo_acc ? dcol + 128u : dcol;
-      for (int kc = 0; kc < p.kchunks; kc++) {
-        const uint32_t slot = mslot, su = mphase;
-        if (++mslot == (uint32_t)p.nslots) {
-          mslot = 0;
-          mphase ^= 1u;
-        }
-        if (!warp_wait(bar(BAR_BFULL + slot), su & 1, wait_ns, abort_flag, p.status)) {
-          ok = false;
-          break;
-        }
-        trace_chunk(tr && li == 1 && lane == 0, 2, kc, 0);
+    // the tile loop, compiled once for sparse and once for dense MMAs (the issue loop is a
+    // latency chain: the MMA form is fixed outside it)
+    auto issue_tiles = [&](auto dense_tag) {
+      constexpr bool kDense = decltype(dense_tag)::value;
+      uint32_t mslot = 0, mphase = 0;  // chunk ring position and wrap parity
+      bool ok = true;
+      for (int li = 0; li < ntiles_cta && ok; li++) {
+        const int acc = li % nacc, use = li / nacc;
+        if (use > 0 && !warp_wait(bar(BAR_AEMPTY + acc), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t blo = dlo0 + slot * slot_step;
-        const uint32_t meta = tmem + meta_col + 8u * (uint32_t)(kc >> 1);
-        const uint32_t idesc_kc = idesc | (uint32_t)(kc & 1);  // sparsity selector
-        const uint32_t a8 = 8u * (uint32_t)kc;
-        const uint64_t b0 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[0]);
-        const uint64_t b1 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[1]);
-        const uint64_t b2 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[2]);
-        const uint64_t b3 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[3]);
-        if (p.dense) {
-          // dense ablation: two K = 16 MMAs per term and chunk (A columns 16kc and 16kc + 8,
-          // B rows 0-15 and 16-31 of the chunk: two core matrices of 16 bytes along K = 2 LBO)
-          const uint64_t bt[4] = {b0, b1, b2, b3};
-#pragma unroll
-          for (int t = 0; t < 4; t++) {
-            if (t < nterms) {
-#pragma unroll
-              for (int h = 0; h < 2; h++) {
-                const uint32_t acc = (h > 0 || kc > 0) ? 1u : (t == 0 ? 0u : (t == 1 && p.lo_acc ? 0u : 1u));
-                mma_dense_elected(t == 0 ? dcol : dcol1, a_term[t] + 16u * (uint32_t)kc + 8u * (uint32_t)h,
-                                  bt[t] + (uint64_t)(h * (2 * kLBO >> 4)), idesc_dense, acc);
+        trace(tr && lane == 0, 1, li, 0);
+        const uint32_t dcol = tmem + (uint32_t)acc * acc_stride;
+        const uint32_t dcol1 = p.lo_acc ? dcol + 128u : dcol;
+        for (int kc = 0; kc < p.kchunks; kc++) {
+          const uint32_t slot = mslot, su = mphase;
+          if (++mslot == (uint32_t)p.nslots) {
+            mslot = 0;
+            mphase ^= 1u;
+          }
+          if (!warp_wait(bar(BAR_BFULL + slot), su & 1, wait_ns, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          trace_chunk(tr && li == 1 && lane == 0, 2, kc, 0);
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t blo = dlo0 + slot * slot_step;
+          const uint32_t meta = tmem + meta_col + 8u * (uint32_t)(kc >> 1);
+          const uint32_t idesc_kc = idesc | (uint32_t)(kc & 1);  // sparsity selector
+          const uint32_t a8 = 8u * (uint32_t)kc;
+          const uint64_t b0 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[0]);
+          const uint64_t b1 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[1]);
+          const uint64_t b2 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[2]);
+          const uint64_t b3 = ((uint64_t)dhi << 32) | (uint64_t)(blo + b_term[3]);
+          if constexpr (kDense) {
+            // dense ablation: two K = 16 MMAs per term and chunk (A columns 16kc and 16kc + 8,
+            // B rows 0-15 and 16-31 of the chunk: two core matrices of 16 bytes along K = 2 LBO)
+            const uint64_t bt[4] = {b0, b1, b2, b3};
+  #pragma unroll
+            for (int t = 0; t < 4; t++) {
+              if (t < nterms) {
+  #pragma unroll
+                for (int h = 0; h < 2; h++) {
+                  const uint32_t acc = (h > 0 || kc > 0) ? 1u : (t == 0 ? 0u : (t == 1 && p.lo_acc ? 0u : 1u));
+                  mma_dense_elected(t == 0 ? dcol : dcol1, a_term[t] + 16u * (uint32_t)kc + 8u * (uint32_t)h,
+                                    bt[t] + (uint64_t)(h * (2 * kLBO >> 4)), idesc_dense, acc);
+                }
               }
             }
+            commit_elected(bar(BAR_BEMPTY + slot));
+          } else {
+            issue_chunk(nterms, dcol, dcol1, a_term[0] + a8, a_term[1] + a8, a_term[2] + a8, a_term[3] + a8, b0, b1, b2,
+                        b3, meta, idesc_kc, kc > 0 ? 1u : 0u, (kc > 0 || !p.lo_acc) ? 1u : 0u, bar(BAR_BEMPTY + slot));
           }
-          commit_elected(bar(BAR_BEMPTY + slot));
-        } else {
-          issue_chunk(nterms, dcol, dcol1, a_term[0] + a8, a_term[1] + a8, a_term[2] + a8, a_term[3] + a8, b0, b1, b2,
-                      b3, meta, idesc_kc, kc > 0 ? 1u : 0u, (kc > 0 || !p.lo_acc) ? 1u : 0u, bar(BAR_BEMPTY + slot));
+          trace_chunk(tr && li == 1 && lane == 0, 2, kc, 1);
         }
-        trace_chunk(tr && li == 1 && lane == 0, 2, kc, 1);
+        if (!ok) break;
+        commit_elected(bar(BAR_AFULL + acc));
+        trace(tr && lane == 0, 1, li, 1);
       }
-      if (!ok) break;
-      commit_elected(bar(BAR_AFULL + acc));
-      trace(tr && lane == 0, 1, li, 1);
-    }
+    };
+    if (p.dense)
+      issue_tiles(std::integral_constant<bool, true>());
+    else
+      issue_tiles(std::integral_constant<bool, false>());
     // every MMA issued above completes before TMEM is released
     commit_elected(bar(BAR_FINAL));
     if (lane == 0) mbar_wait(bar(BAR_FINAL), 0, kDrainNs, nullptr, p.status);
