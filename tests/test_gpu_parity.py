@@ -291,6 +291,25 @@ def test_full_size_box3d27p_sampled(torch_cuda, oracle_mod):
     assert np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2)) <= 1e-5
 
 
+@pytest.mark.parametrize("name,npts", [("star2d13p_8192", 3), ("box2d49p_8192", 2)])
+def test_full_size_c4_sampled(torch_cuda, oracle_mod, name, npts):
+    """Star-2D13P / Box-2D49P 8192^2, 200 steps, Gaussian weights, periodic, in the suite's
+    launch configuration (autotuned fusion depth), single-word and split BF16: sampled points
+    against the dependence-cone oracle (a few seconds of FP64 work per point)."""
+    cfg = inputs.CONFIGS[name]
+    w = inputs.stencil_weights(cfg["shape"], 2, cfg["radius"], cfg["recipe"], seed=cfg["seed"])
+    u = inputs.make_grid(cfg["grid"], cfg["seed"], cfg["dims"])
+    rng = np.random.default_rng(5)
+    pts = [tuple(int(rng.integers(0, d)) for d in cfg["dims"]) for _ in range(npts - 1)] + [(0, 8191)]
+    u64 = u.astype(np.float64)
+    ref = np.array([oracle_mod.point(u64, w, cfg["bc"], cfg["steps"], p) for p in pts])
+    for dtype in ("bf16", "bf16_split"):
+        got, plan = _run_sparse(torch_cuda, u, w, cfg["steps"], dtype, cfg["bc"], 0, cfg["shape"])
+        vals = np.array([got[p] for p in pts])
+        l2 = np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2))
+        assert l2 <= TOL[dtype], (dtype, plan.info().fusion_depth, l2)
+
+
 def test_full_size_heat3d_sampled(torch_cuda, oracle_mod):
     """Heat-3D 7-point star 512^3 with random weights, zero Dirichlet boundary, 50 steps on
     zero-mean data, FP16 split operands (low-order accumulator by default): sampled points,
