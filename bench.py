@@ -499,7 +499,7 @@ def _rel_l2_gpu(binding, x, ref):
 
 
 def suite_mode():
-    """Configs C1, C3, C4a/b: GStencil/s of the sparse path (single and split, fusion depth
+    """Configs C1, C3, C4a/b and the 1D workloads: GStencil/s of the sparse path (single and split, fusion depth
     autotuned) and of the plain FP32 direct kernel, with rel-L2 against the FP64 oracle (C1:
     full grid; C3: sampled points, plus the whole grid against the FP32 direct result) or
     against the FP32 direct result (C4)."""
@@ -509,7 +509,7 @@ def suite_mode():
     import oracle
     from paper_2506_22969_gb300 import binding, inputs
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for name in ("heat2d_512", "star2d13p_8192", "box2d49p_8192", "box3d27p_256", "heat3d_512"):
+    for name in ("heat2d_512", "star2d13p_8192", "box2d49p_8192", "box3d27p_256", "heat3d_512", "heat1d", "1d5p"):
         cfg = inputs.CONFIGS[name]
         dims, T, bc = cfg["dims"], cfg["steps"], cfg["bc"]
         w = inputs.stencil_weights(cfg["shape"], cfg["ndim"], cfg["radius"], cfg["recipe"], seed=cfg["seed"])
@@ -523,9 +523,9 @@ def suite_mode():
         ms_d, _ = _time_runs(lambda: binding.direct_run(w, x, ref_gpu, work, T, bc=bc), 2, 1, flush)
         line["fp32_direct_gstencil_s"] = pts / ms_d / 1e6
         sample, sample_ref = None, None
-        if cfg["ndim"] == 3:
-            # 3D: sampled points against the FP64 oracle's dependence cones, and the whole grid
-            # against the FP32 direct kernel
+        if cfg["ndim"] != 2:
+            # 1D and 3D: sampled points against the FP64 oracle's dependence cones, and the
+            # whole grid against the FP32 direct kernel
             rng = np.random.default_rng(0)
             sample = [tuple(int(rng.integers(0, d)) for d in dims) for _ in range(6)]
             u64 = u.astype(np.float64)
@@ -542,6 +542,8 @@ def suite_mode():
             dtypes = ("fp16",)
         elif cfg["ndim"] == 3:
             dtypes = ("fp16", "bf16", "fp16_split", "bf16_split")
+        elif cfg["ndim"] == 1:
+            dtypes = ("bf16", "bf16_split")
         else:
             dtypes = ("bf16", "bf16_split")
         full_ref = oracle.run(u, w, bc, T) if name == "heat2d_512" else None

@@ -51,6 +51,37 @@ __global__ void pad_copy2d_kernel(const float* __restrict__ in, float* __restric
   fold_maxabs(maxabs, m);
 }
 
+__global__ void pad_copy1d_kernel(const float* __restrict__ in, float* __restrict__ out, int64_t W, int G,
+                                  int64_t Wp, int periodic, unsigned* maxabs) {
+  float m = 0.f;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < Wp; i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t xp = i0 + threadIdx.x;
+    if (xp >= Wp) continue;
+    int64_t x = xp - G;
+    float v = 0.f;
+    if (xp < W + 2 * G) {
+      if (periodic) {
+        x = x < 0 ? x + W : (x >= W ? x - W : x);
+        v = in[x];
+      } else if (x >= 0 && x < W) {
+        v = in[x];
+      }
+    }
+    out[xp] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+  fold_maxabs(maxabs, m);
+}
+
+// Periodic 1D ghosts: cell i < G holds x = i - G, the image of x + W; cell W + G + i holds
+// x = W + i, the image of i.
+__global__ void ghost_refresh1d_kernel(float* line, int64_t W, int G) {
+  for (int i = threadIdx.x; i < G; i += blockDim.x) {
+    line[i] = line[i + W];
+    line[W + G + i] = line[G + i];
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Plain FP32 direct stencil: each CTA stages a (TY + 2r) x (TX + 2r) [x (TZ + 2r)] input
 // tile in shared memory (coalesced loads, boundary rule applied on load) and each thread
@@ -108,6 +139,37 @@ __global__ void __launch_bounds__(256) direct2d_kernel(const __grid_constant__ D
   for (int k = 0; k < DSTRIP; k++) {
     const int64_t y = y0 + ch * DSTRIP + k, x = x0 + cx;
     if (y < H && x < W) out[y * W + x] = acc[k];
+  }
+}
+
+// 1D: a CTA covers 2048 outputs; each thread computes 8 of them, 256 apart (coalesced), in
+// the fixed offset order.
+constexpr int E1X = 2048;
+
+template <int R>
+__global__ void __launch_bounds__(256) direct1d_kernel(const __grid_constant__ DirectParams p,
+                                                       const float* __restrict__ in, float* __restrict__ out) {
+  __shared__ float tile[E1X + 2 * R];
+  const int64_t W = p.W, x0 = (int64_t)blockIdx.x * E1X;
+  for (int i = threadIdx.x; i < E1X + 2 * R; i += blockDim.x) {
+    int64_t x = x0 + i - R;
+    float v = 0.f;
+    if (p.periodic) {
+      x = x < 0 ? x + W : (x >= W ? x - W : x);
+      v = in[x];
+    } else if (x >= 0 && x < W) {
+      v = in[x];
+    }
+    tile[i] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < E1X / 256; k++) {
+    const int lx = (int)threadIdx.x + 256 * k;
+    float acc = 0.f;
+#pragma unroll
+    for (int d = 0; d < 2 * R + 1; d++) acc = fmaf(p.wdense[d], tile[lx + d], acc);
+    if (x0 + lx < W) out[x0 + lx] = acc;
   }
 }
 
@@ -375,6 +437,19 @@ cudaError_t launch_ghost_refresh3d(float* padded, int D, int H, int W, int G, in
   return cudaGetLastError();
 }
 
+cudaError_t launch_pad_copy1d(const float* in, float* out, int64_t W, int G, int64_t Wp, int periodic,
+                              unsigned* maxabs, cudaStream_t stream) {
+  int64_t blocks = (Wp + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  pad_copy1d_kernel<<<(unsigned)blocks, 256, 0, stream>>>(in, out, W, G, Wp, periodic, maxabs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ghost_refresh1d(float* line, int64_t W, int G, cudaStream_t stream) {
+  ghost_refresh1d_kernel<<<1, 64, 0, stream>>>(line, W, G);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pad_copy2d(const float* in, float* padded, int H, int W, int G, int64_t Wp, int periodic,
                               unsigned* maxabs, cudaStream_t stream) {
   const int64_t total = ((int64_t)H + 2 * G) * Wp;
@@ -420,8 +495,23 @@ cudaError_t launch_band2d(BandParams p, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+template <int R>
+static cudaError_t launch_direct1d(const DirectParams& p, const float* in, float* out, cudaStream_t stream) {
+  direct1d_kernel<R><<<(unsigned)((p.W + E1X - 1) / E1X), 256, 0, stream>>>(p, in, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* out, cudaStream_t stream) {
   const int r = p.radius;
+  if (p.ndim == 1) {
+    switch (r) {
+      case 1: return launch_direct1d<1>(p, in, out, stream);
+      case 2: return launch_direct1d<2>(p, in, out, stream);
+      case 3: return launch_direct1d<3>(p, in, out, stream);
+      case 4: return launch_direct1d<4>(p, in, out, stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (p.ndim == 2) {
     switch (r) {
       case 1: return launch_direct2d<1>(p, in, out, stream);

@@ -21,6 +21,7 @@
 using spst::PlanGeometry;
 using spst::SweepTables;
 using spst::Tile2D;
+using spst::Tile1D;
 using spst::Tile3D;
 
 namespace {
@@ -180,6 +181,22 @@ std::string plan_geometry(sparstencil_plan_t p) {
   const bool d3 = g.ndim == 3;
   g.G = p->t_max * p->radius;
   if (g.G > 60) return "fused radius too large";
+  if (g.ndim == 1) {
+    // the padded line (G ghost cells each side) is read as rows of Tile1D::ROW floats; a
+    // tile's halo is the whole rows covering its 16384 outputs and 2G ghosts
+    if (g.W < 2 * g.G || g.W < 4) return "grid smaller than twice the fused radius";
+    if (g.W > (1ll << 30)) return "grid extent too large";
+    g.Dp = g.Hp = 1;
+    g.Wp = (g.W + 2 * g.G + Tile1D::ROW - 1) / Tile1D::ROW * Tile1D::ROW;
+    g.P = Tile1D::ROW;
+    g.box_h = (Tile1D::TX + 2 * g.G + Tile1D::ROW - 1) / Tile1D::ROW;
+    g.box_d = 1;
+    g.tiles_x = (g.W + Tile1D::TX - 1) / Tile1D::TX;
+    g.tiles_y = g.tiles_z = 1;
+    g.num_tiles = g.tiles_x;
+    if (g.num_tiles > (1ll << 30)) return "too many tiles";
+    return "";
+  }
   if (g.H < 2 * g.G || g.W < 2 * g.G || g.W < 4 || (d3 && g.D < 2 * g.G))
     return "grid smaller than twice the fused radius";
   if (g.H > (1 << 30) || g.W > (1 << 30) || g.D > (1 << 30)) return "grid extent too large";
@@ -253,7 +270,15 @@ sparstencil_status make_tmaps(sparstencil_plan_t p) {
   const PlanGeometry& g = p->geo;
   for (int i = 0; i < 2; i++) {
     CUresult r;
-    if (g.ndim == 3) {
+    if (g.ndim == 1) {
+      cuuint64_t gdim[2] = {(cuuint64_t)Tile1D::ROW, (cuuint64_t)(g.Wp / Tile1D::ROW)};
+      cuuint64_t gstr[1] = {(cuuint64_t)Tile1D::ROW * 4};
+      cuuint32_t box[2] = {(cuuint32_t)g.P, (cuuint32_t)g.box_h};
+      cuuint32_t es[2] = {1, 1};
+      r = enc(&p->tmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->pad(i), gdim, gstr, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else if (g.ndim == 3) {
       cuuint64_t gdim[3] = {(cuuint64_t)g.Wp, (cuuint64_t)g.Hp, (cuuint64_t)g.Dp};
       cuuint64_t gstr[2] = {(cuuint64_t)g.Wp * 4, (cuuint64_t)g.Wp * (cuuint64_t)g.Hp * 4};
       cuuint32_t box[3] = {(cuuint32_t)g.P, (cuuint32_t)g.box_h, (cuuint32_t)g.box_d};
@@ -341,6 +366,7 @@ spst::Sweep2DParams sweep_params(sparstencil_plan_t p, const SweepTables& T, con
   prm.W = (int)g.W;
   prm.D = (int)g.D;
   prm.dim3 = g.ndim == 3 ? 1 : 0;
+  prm.dim1 = g.ndim == 1 ? 1 : 0;
   prm.G = g.G;
   prm.tiles_x = (int)g.tiles_x;
   prm.tiles_y = (int)g.tiles_y;
@@ -400,6 +426,7 @@ cudaError_t copy_in(sparstencil_plan_t p, const float* in, float* pad, int64_t s
     const double growth = std::pow(std::max(sabs, 1.0), (double)steps);
     p->growth = (float)std::min(growth, 1e30);
   }
+  if (g.ndim == 1) return spst::launch_pad_copy1d(in, pad, g.W, g.G, g.Wp, periodic, maxabs, stream);
   if (g.ndim == 3)
     return spst::launch_pad_copy3d(in, pad, (int)g.D, (int)g.H, (int)g.W, g.G, g.Wp, periodic, maxabs, stream);
   return spst::launch_pad_copy2d(in, pad, (int)g.H, (int)g.W, g.G, g.Wp, periodic, maxabs, stream);
@@ -422,6 +449,10 @@ void set_output(sparstencil_plan_t p, spst::Sweep2DParams* prm, float* pad, floa
 cudaError_t after_sweep(sparstencil_plan_t p, int depth, const float* src, const spst::Sweep2DParams& prm, bool last,
                         cudaStream_t stream) {
   const PlanGeometry& g = p->geo;
+  if (g.ndim == 1) {
+    if (last || p->bc != SPST_PERIODIC) return cudaSuccess;
+    return spst::launch_ghost_refresh1d(prm.out, g.W, g.G, stream);
+  }
   if (g.ndim == 3) {
     if (last || p->bc != SPST_PERIODIC) return cudaSuccess;
     return spst::launch_ghost_refresh3d(prm.out, (int)g.D, (int)g.H, (int)g.W, g.G, g.Wp, stream);
@@ -690,7 +721,7 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   if (bc != SPST_DIRICHLET_ZERO && bc != SPST_PERIODIC) return fail(SPST_ERR_INVALID, "bad boundary");
   if (radius < 1) return fail(SPST_ERR_INVALID, "radius must be >= 1");
   if (fusion_depth < 0) return fail(SPST_ERR_INVALID, "fusion_depth must be >= 0");
-  if (ndim != 2 && ndim != 3) return fail(SPST_ERR_UNSUPPORTED, "ndim must be 2 or 3");
+  if (ndim < 1 || ndim > 3) return fail(SPST_ERR_UNSUPPORTED, "ndim must be 1, 2 or 3");
   for (int i = 0; i < ndim; i++)
     if (dims[i] <= 0) return fail(SPST_ERR_INVALID, "grid extents must be positive");
   if (!shape_mask_ok(shape, ndim, radius, weights))
@@ -704,19 +735,21 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   p->bc = bc;
   p->requested_t = fusion_depth;
   p->t = fusion_depth == 0 ? 1 : fusion_depth;
-  if (bc == SPST_DIRICHLET_ZERO && p->t > 1 && (radius > 4 || ndim == 3))
+  if (bc == SPST_DIRICHLET_ZERO && p->t > 1 && (radius > 4 || ndim != 2))
     return fail(SPST_ERR_UNSUPPORTED, "temporal fusion with a Dirichlet boundary needs a 2D grid and radius <= 4");
   p->t_max = p->t;
   // fusion_depth 0: the deepest of 3, 2, 1 whose tables fit is planned; the first run times
   // every depth up to it and keeps the fastest per time step
-  const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && (radius > 4 || ndim == 3)) ? 1 : 3) : p->t;
+  // 1D: K grows by only 2r columns per fused step (k' = kt + 127), so deeper fusion is searched
+  const int t_deep = ndim == 1 ? std::max(1, std::min(8, 60 / radius)) : 3;
+  const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && (radius > 4 || ndim != 2)) ? 1 : t_deep) : p->t;
   const int side = 2 * radius + 1;
-  p->w64.resize((size_t)side * side * (ndim == 3 ? side : 1));
+  p->w64.resize((size_t)side * (ndim >= 2 ? side : 1) * (ndim == 3 ? side : 1));
   for (size_t i = 0; i < p->w64.size(); i++) p->w64[i] = (double)weights[i];
   PlanGeometry& g = p->geo;
   g.ndim = ndim;
   g.D = ndim == 3 ? dims[0] : 1;
-  g.H = dims[ndim - 2];
+  g.H = ndim >= 2 ? dims[ndim - 2] : 1;
   g.W = dims[ndim - 1];
   std::string err;
   for (int tm = t_try; tm >= 1; tm--) {
@@ -1049,20 +1082,20 @@ sparstencil_status sparstencil_direct_run(int radius, const float* weights, int 
                                           sparstencil_boundary bc, const float* in, float* out, float* work,
                                           int64_t timesteps, cudaStream_t stream) {
   if (!weights || !dims || !in || !out || !work) return fail(SPST_ERR_INVALID, "null argument");
-  if (ndim != 2 && ndim != 3) return fail(SPST_ERR_UNSUPPORTED, "ndim must be 2 or 3");
-  if (radius < 1 || (ndim == 2 && radius > 4) || (ndim == 3 && radius > 3))
+  if (ndim < 1 || ndim > 3) return fail(SPST_ERR_UNSUPPORTED, "ndim must be 1, 2 or 3");
+  if (radius < 1 || (ndim <= 2 && radius > 4) || (ndim == 3 && radius > 3))
     return fail(SPST_ERR_UNSUPPORTED, "radius out of range");
   if (timesteps < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
   spst::DirectParams prm;
   std::memset(&prm, 0, sizeof(prm));
   prm.ndim = ndim;
   prm.D = ndim == 3 ? dims[0] : 1;
-  prm.H = dims[ndim - 2];
+  prm.H = ndim >= 2 ? dims[ndim - 2] : 1;
   prm.W = dims[ndim - 1];
   prm.radius = radius;
   prm.periodic = bc == SPST_PERIODIC ? 1 : 0;
   const int side = 2 * radius + 1;
-  int total = ndim == 3 ? side * side * side : side * side;
+  int total = ndim == 3 ? side * side * side : (ndim == 2 ? side * side : side);
   for (int idx = 0; idx < total; idx++) {
     if (weights[idx] == 0.f) continue;
     if (prm.npts >= 343) return fail(SPST_ERR_UNSUPPORTED, "too many stencil points");
@@ -1077,9 +1110,9 @@ sparstencil_status sparstencil_direct_run(int radius, const float* weights, int 
     prm.w[prm.npts] = weights[idx];
     prm.npts++;
   }
-  if (ndim == 2 || radius == 1)
+  if (ndim <= 2 || radius == 1)
     for (int idx = 0; idx < total; idx++) prm.wdense[idx] = weights[idx];
-  if (prm.H < radius || prm.W < radius || prm.D < (ndim == 3 ? radius : 1))
+  if (prm.H < (ndim >= 2 ? radius : 1) || prm.W < radius || prm.D < (ndim == 3 ? radius : 1))
     return fail(SPST_ERR_UNSUPPORTED, "grid smaller than the radius");
   const size_t bytes = (size_t)prm.D * prm.H * prm.W * 4;
   if (timesteps == 0) {

@@ -24,6 +24,7 @@ struct Sweep2DParams {
   int H, W;             // true grid extents (rows, columns)
   int D;                // planes (3D; 1 for 2D)
   int dim3;             // 1: 3D sweep (Tile3D patches and tiles, 3D TMA box)
+  int dim1;             // 1: 1D sweep (Tile1D patches and tiles, rows of the 2D view of the line)
   int G;                // ghost width of the input padded grid
   int tiles_x, tiles_y, tiles_z, num_tiles;
   int P, box_h, box_d;  // shared-memory tile pitch (floats), height (rows), depth (planes) = TMA box
@@ -96,8 +97,14 @@ struct DirectParams {
   int npts;
   int off[343][3];      // offsets (z, y, x) of the nonzero weights
   float w[343];         // their weights (FP32 FMAs in this order)
-  float wdense[81];     // the dense cube (zeros included): 2D (2r+1)^2 for r <= 4, 3D 27 for r = 1
+  float wdense[81];     // the dense cube (zeros included): 1D 2r+1 and 2D (2r+1)^2 for r <= 4, 3D 27 for r = 1
 };
+// 1D copy-in of a line of W cells into its padded copy (G ghost cells each side, length Wp),
+// periodic images or zeros in the ghosts, and max |in| into *maxabs when it is not null.
+cudaError_t launch_pad_copy1d(const float* in, float* out, int64_t W, int G, int64_t Wp, int periodic,
+                              unsigned* maxabs, cudaStream_t stream);
+// Periodic 1D: copies the wrapped images into the G ghost cells at each end of a padded line.
+cudaError_t launch_ghost_refresh1d(float* line, int64_t W, int G, cudaStream_t stream);
 // One FP32 CUDA-core step in -> out.
 cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* out, cudaStream_t stream);
 

@@ -569,21 +569,23 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
                                   int max_pieces, bool drop_zero_pairs, SweepTables* out) {
   SweepTables& T = *out;
   T = SweepTables();
-  const bool d3 = geo.ndim == 3;
-  T.ndim = d3 ? 3 : 2;
+  const bool d3 = geo.ndim == 3, d1 = geo.ndim == 1;
+  T.ndim = geo.ndim;
   T.R = R;
   T.kt = 2 * R + 1;
   const int kt = T.kt;
-  const int r1 = d3 ? Tile3D::R1 : Tile2D::R1, r2 = d3 ? Tile3D::R2 : Tile2D::R2, r3 = d3 ? Tile3D::R3 : 1;
-  const int M = d3 ? Tile3D::M : Tile2D::M;
+  // 1D: one staircase block (r2 = r3 = 1), so the 2D formulas below hold with mb = 1
+  const int r1 = d1 ? Tile1D::R1 : (d3 ? Tile3D::R1 : Tile2D::R1);
+  const int r2 = d1 ? 1 : (d3 ? Tile3D::R2 : Tile2D::R2), r3 = d3 ? Tile3D::R3 : 1;
+  const int M = d1 ? Tile1D::M : (d3 ? Tile3D::M : Tile2D::M);
   T.r1 = r1;
   T.r2 = r2;
   T.r3 = r3;
   T.g = kt + r1 - 1;
-  T.mb = kt + r2 - 1;
+  T.mb = d1 ? 1 : kt + r2 - 1;
   T.mz = d3 ? kt + r3 - 1 : 1;
   T.kprime = T.g * T.mb * T.mz;
-  if ((int)wfused.size() != (d3 ? kt * kt * kt : kt * kt)) return "fused weight cube has the wrong size";
+  if ((int)wfused.size() != (d3 ? kt * kt * kt : (d1 ? kt : kt * kt))) return "fused weight cube has the wrong size";
   T.wfused = wfused;
   T.wfused32.resize(wfused.size());
   double S = 0.0;
@@ -677,6 +679,7 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   auto off = [&](int col) {
     const int c = col % g, u = (col / g) % mb, v = col / (g * mb);
     const int plane = geo.box_h * geo.P;
+    if (d1) return c + geo.G - R;  // the line is contiguous in the tile
     return (d3 ? (v + geo.G - R) * plane : 0) + (u + geo.G - R) * geo.P + (c + geo.G - R);
   };
   std::vector<std::pair<int, int>> offs;

@@ -26,6 +26,17 @@ struct Tile2D {
   static constexpr int KCHUNK = 32;   // logical K per tcgen05.mma.sp (kind::f16)
 };
 
+// Geometry of the 1D sweep kernel: a patch is R1 = 128 consecutive outputs (M = 128 rows); a
+// CTA tile is N = 128 patches = 16384 outputs.  The padded line is read through a 2D view of
+// rows of ROW floats, so a tile's halo is one TMA box of whole rows.
+struct Tile1D {
+  static constexpr int R1 = 128;
+  static constexpr int N = 128;
+  static constexpr int M = R1;
+  static constexpr int TX = N * R1;  // 16384
+  static constexpr int ROW = 256;    // floats per row of the 2D view
+};
+
 // Geometry of the 3D sweep kernel: a patch is R1 x R2 x R3 = 8 x 4 x 4 outputs (x, y, z),
 // M = 128 rows; a CTA tile is NX x NY x NZ = 8 x 4 x 4 patches = 64 x 16 x 16 outputs,
 // N = 128 columns.

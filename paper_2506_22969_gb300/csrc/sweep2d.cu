@@ -304,17 +304,21 @@ constexpr int BAR_COUNT = BAR_FINAL + 1;  // 29 barriers = 232 bytes, below the 
 static_assert(BAR_COUNT * 8 <= 256, "barrier area overlaps the TMEM slot");
 constexpr uint32_t TMEM_COLS = 512;
 
+constexpr int k1dTile = 16384, k1dRow = 256;  // 1D: outputs per tile, floats per row of the 2D view
 constexpr int kGatherWarp0 = 4 + kEpiWarps;                     // the last 16 warps build B''
 constexpr int kGatherWarps = kSweepThreads / 32 - kGatherWarp0;  // 16
 constexpr int kItems = 64 / kGatherWarps;                        // patch pairs per gather warp per chunk
 
-// DIM3 = 0: 2D sweep (Tile2D: 16 x 8 patches, 128 x 128 tiles); DIM3 = 1: 3D sweep (Tile3D:
+// DIM = 1: 1D sweep (patches of 128 consecutive outputs, tiles of 128 patches read as whole
+// rows of a 2D view of the padded line); DIM = 2: 2D sweep (Tile2D: 16 x 8 patches, 128 x 128
+// tiles); DIM = 3: 3D sweep (Tile3D:
 // 8 x 4 x 4 patches, 64 x 16 x 16 tiles).  Patch n of a 3D tile, with n = a*16 + h*8 + b, is
 // (px, py, pz) = (4(a&1) + 2h + (b&1), b>>1, a>>1): the two half-warps of a gather warp take
 // patches n and n+8, 16 words apart in x, as in 2D.
-template <int FP16, int SPLIT, int DIM3>
+template <int FP16, int SPLIT, int DIM>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep2d_kernel(const __grid_constant__ CUtensorMap tmap_in, const Sweep2DParams p) {
+  constexpr bool DIM3 = DIM == 3, DIM1 = DIM == 1;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -459,7 +463,14 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         const uint32_t dst = sbase + (uint32_t)stage * L.halo_stride;
         trace(tr, 0, li, 0);
         mbar_expect_tx(bar(BAR_HFULL + stage), bytes);
-        if (DIM3) {
+        if (DIM1) {
+          // whole rows of the 2D view of the padded line: tile tt starts at row tt * 64
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                  dst),
+              "l"(&tmap_in), "r"(0), "r"(tt * (k1dTile / k1dRow)), "r"(bar(BAR_HFULL + stage))
+              : "memory");
+        } else if (DIM3) {
           const int tx = tt % p.tiles_x, ty = (tt / p.tiles_x) % p.tiles_y, tz = tt / (p.tiles_x * p.tiles_y);
           asm volatile(
               "cp.async.bulk.tensor.3d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
@@ -598,6 +609,57 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;");
       trace(tr && warp == 4 && lane == 0, 3, li, 0);
       const int tt = (int)blockIdx.x + li * (int)gridDim.x;
+      if (DIM1) {
+        // column n of the accumulator is patch n: outputs x0 + 128n + rho, a lane per output
+        const int64_t x0 = (int64_t)tt * k1dTile;
+        const bool full1 = x0 + k1dTile <= p.W;
+        float* ob = p.out + G + x0 + rho;
+#pragma unroll 1
+        for (int cg = cg0; cg < cg0 + kGroups; cg++) {
+          uint32_t v[16];
+          const uint32_t acc_addr = lane_addr + (uint32_t)acc * acc_stride + (uint32_t)(cg * 16);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(acc_addr));
+          if (SPLIT && p.lo_acc) {
+            uint32_t l[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7]),
+                  "=r"(l[8]), "=r"(l[9]), "=r"(l[10]), "=r"(l[11]), "=r"(l[12]), "=r"(l[13]), "=r"(l[14]), "=r"(l[15])
+                : "r"(acc_addr + 128u));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(l[j]));
+          }
+          float c[16];
+          const uint32_t ca = cv_s + (uint32_t)((li & 1) * 128 + cg * 16) * 4u;
+#pragma unroll
+          for (int k4 = 0; k4 < 4; k4++) {
+            const float4 c4 = lds_v4_f32(ca + 16u * k4);
+            c[4 * k4] = c4.x;
+            c[4 * k4 + 1] = c4.y;
+            c[4 * k4 + 2] = c4.z;
+            c[4 * k4 + 3] = c4.w;
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const int n = cg * 16 + j;
+            const float val = fmaf(c[j], p.S_lo, fmaf(c[j], p.S_hi, __uint_as_float(v[j]) * out_scale));
+            if (full1 || x0 + n * 128 + rho < p.W) ob[n * 128] = val;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(bar(BAR_AEMPTY + acc));
+          mbar_arrive(bar(BAR_CVEMPTY + (li & 1)));
+        }
+        continue;
+      }
       const int tx = tt % p.tiles_x, ty = DIM3 ? (tt / p.tiles_x) % p.tiles_y : tt / p.tiles_x;
       const int x0 = tx * (DIM3 ? 64 : 128), y0 = ty * (DIM3 ? 16 : 128);
       const int z0 = DIM3 ? (tt / (p.tiles_x * p.tiles_y)) * 16 : 0;
@@ -709,7 +771,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       const int pp = gw + kGatherWarps * i;
       const int n = (pp >> 3) * 16 + (pp & 7) + 8 * h;
       n_i[i] = n;
-      if (DIM3) {
+      if (DIM1) {
+        base_i[i] = 4 * (n * 128);  // patch n: outputs 128n .. 128n+127 of the tile
+      } else if (DIM3) {
         const int a = n >> 4, b = n & 7;
         const int px = ((a & 1) << 2) | (h << 1) | (b & 1), py = b >> 1, pz = a >> 1;
         base_i[i] = 4 * (pz * 4 * p.box_h * P + py * 4 * P + px * 8);
@@ -724,7 +788,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     // 2D row, then two bits of column)
     const int sm = pl & 7;
     const uint32_t c_off =
-        4u * (uint32_t)(DIM3 ? (sm >> 2) * p.box_h * P + ((sm >> 1) & 1) * P + (sm & 1) : (sm >> 2) * P + (sm & 3));
+        4u * (uint32_t)(DIM1 ? sm
+                             : DIM3 ? (sm >> 2) * p.box_h * P + ((sm >> 1) & 1) * P + (sm & 1) : (sm >> 2) * P + (sm & 3));
     for (int li = 0; li < ntiles_cta; li++) {
       const int stage = li & 1;
       if (!warp_wait(bar(BAR_HFULL + stage), (li >> 1) & 1, wait_ns, abort_flag, p.status)) break;
@@ -743,8 +808,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         // The 16 lanes of a half-warp share the patch: lane pl loads sample pl mod 8 and an
         // xor butterfly over 8 lanes sums them (the same sum in every lane: each level adds
         // the same two partial sums, and FP32 addition is commutative).
-        const uint32_t m0 = ba[i] + 4u * (uint32_t)(DIM3 ? (G + 1) * p.box_h * P + (G + 1) * P + G + 3
-                                                         : (G + 3) * P + G + 6);
+        const uint32_t m0 = ba[i] + 4u * (uint32_t)(DIM1 ? G + 60
+                                                         : DIM3 ? (G + 1) * p.box_h * P + (G + 1) * P + G + 3
+                                                                : (G + 3) * P + G + 6);
         float cs = lds_f32(m0 + c_off);
         cs += __shfl_xor_sync(0xffffffffu, cs, 1);
         cs += __shfl_xor_sync(0xffffffffu, cs, 2);
@@ -914,10 +980,12 @@ cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p_in
     if (need > (size_t)L.off_lut) return cudaErrorInvalidConfiguration;
   }
   const size_t smem = sweep2d_smem_bytes(p);
-  auto kern = p.dim3 ? (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 1> : sweep2d_kernel<1, 0, 1>)
-                              : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 1> : sweep2d_kernel<0, 0, 1>))
-                     : (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 0> : sweep2d_kernel<1, 0, 0>)
-                              : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 0> : sweep2d_kernel<0, 0, 0>));
+  auto kern = p.dim3   ? (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 3> : sweep2d_kernel<1, 0, 3>)
+                                 : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 3> : sweep2d_kernel<0, 0, 3>))
+              : p.dim1 ? (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 1> : sweep2d_kernel<1, 0, 1>)
+                                 : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 1> : sweep2d_kernel<0, 0, 1>))
+                       : (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 2> : sweep2d_kernel<1, 0, 2>)
+                                 : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 2> : sweep2d_kernel<0, 0, 2>));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;

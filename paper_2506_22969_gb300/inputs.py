@@ -96,6 +96,10 @@ def stencil_weights(shape: str, ndim: int, radius: int, recipe: str, seed: int =
 
 # The paper's workloads restated as single-run configurations (Table 2 shapes).
 CONFIGS = {
+    "heat1d": dict(name="Heat-1D 3-point 10240000, periodic, 10000 steps", shape="star", ndim=1, radius=1,
+                   recipe="heat", dims=(10240000,), steps=10000, bc="periodic", grid="u01", seed=6),
+    "1d5p": dict(name="1D5P 5-point 10240000, periodic, 10000 steps", shape="box", ndim=1, radius=2,
+                 recipe="random", dims=(10240000,), steps=10000, bc="periodic", grid="u01", seed=7),
     "heat2d_512": dict(name="Heat-2D 5-point star 512^2, Dirichlet zero, 8 steps", shape="star", ndim=2, radius=1,
                        recipe="heat", dims=(512, 512), steps=8, bc="dirichlet", grid="u01", seed=1),
     "box2d9p_4096": dict(name="Box-2D 9-point 4096^2, periodic, 100 steps", shape="box", ndim=2, radius=1,

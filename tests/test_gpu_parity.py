@@ -370,3 +370,58 @@ def test_dense_ablation_matches_oracle(torch_cuda, oracle_mod, ndim, shape, r, r
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
     assert l2 <= TOL[dtype], (l2, linf)
+
+
+CASES_1D = [
+    # (shape, r, recipe, length, steps, bc, dtype, t): 1D sweep (patches of 128 outputs, tiles
+    # of 16384), ragged, sub-tile and multi-tile lengths
+    ("star", 1, "heat", 100000, 20, "dirichlet", "fp16", 1),
+    ("star", 1, "heat", 3 * 16384 + 100, 30, "periodic", "bf16_split", 4),
+    ("box", 2, "random", 50000, 12, "periodic", "bf16", 3),
+    ("box", 2, "random", 70000, 9, "dirichlet", "fp16_split", 1),
+    ("star", 1, "random", 300, 5, "periodic", "bf16", 1),
+    ("box", 3, "gaussian", 40000, 16, "periodic", "bf16_split", 0),
+]
+
+
+@pytest.mark.parametrize("shape,r,recipe,length,steps,bc,dtype,t", CASES_1D)
+def test_sparse_1d_matches_oracle(torch_cuda, oracle_mod, shape, r, recipe, length, steps, bc, dtype, t):
+    w = inputs.stencil_weights(shape, 1, r, recipe, seed=15)
+    u = inputs.uniform01(9, (length,))
+    ref = oracle_mod.run(u, w, bc, steps)
+    got, plan = _run_sparse(torch_cuda, u, w, steps, dtype, bc, t, shape)
+    assert plan.info().ndim == 1
+    l2, linf = oracle_mod.rel_errors(got, ref)
+    assert np.all(np.isfinite(got))
+    assert l2 <= TOL[dtype], (l2, linf, plan.info().fusion_depth)
+
+
+def test_closed_form_fourier_mode_1d(torch_cuda):
+    """Periodic 1D with random weights, fused 8 steps per sweep: u = 1/2 + cos(theta x) / 2
+    gives u_T = S^T / 2 + Re(lambda^T e^{i theta x}) / 2 with lambda = sum_o w[o] e^{i theta o}."""
+    L, T = 5 * 16384 + 4096, 200
+    w = inputs.stencil_weights("box", 1, 2, "random", seed=16).astype(np.float64)
+    th = 2 * np.pi * 7 / L
+    x = np.arange(L)
+    lam = sum(w[o + 2] * np.exp(1j * th * o) for o in range(-2, 3))
+    u0 = (0.5 + 0.5 * np.cos(th * x)).astype(np.float32)
+    ref = 0.5 * float(np.sum(w)) ** T + 0.5 * np.real(lam ** T * np.exp(1j * th * x))
+    got, plan = _run_sparse(torch_cuda, u0, w.astype(np.float32), T, "bf16_split", "periodic", 8, "box")
+    assert plan.info().fusion_depth == 8
+    assert np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2)) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["heat1d", "1d5p"])
+def test_full_size_1d_sampled(torch_cuda, oracle_mod, name):
+    """Heat-1D / 1D5P at the paper's size (10,240,000 points, 10,000 steps, periodic), in the
+    suite's launch configuration (autotuned depth), split BF16: sampled points against the
+    dependence-cone oracle."""
+    cfg = inputs.CONFIGS[name]
+    w = inputs.stencil_weights(cfg["shape"], 1, cfg["radius"], cfg["recipe"], seed=cfg["seed"])
+    u = inputs.make_grid(cfg["grid"], cfg["seed"], cfg["dims"])
+    got, plan = _run_sparse(torch_cuda, u, w, cfg["steps"], "bf16_split", cfg["bc"], 0, cfg["shape"])
+    pts = [(0,), (5120000,), (10239999,)]
+    u64 = u.astype(np.float64)
+    ref = np.array([oracle_mod.point(u64, w, cfg["bc"], cfg["steps"], p) for p in pts])
+    vals = np.array([got[p] for p in pts])
+    assert np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2)) <= 1e-5, plan.info().fusion_depth

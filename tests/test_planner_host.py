@@ -349,6 +349,54 @@ def test_cost_model_entry_point(lib):
         assert e.value.code == 1
 
 
+@pytest.mark.parametrize("shape,r,t,dtype", [("star", 1, 1, "bf16_split"), ("box", 2, 1, "bf16"),
+                                           ("star", 1, 4, "fp16_split"), ("box", 2, 3, "bf16_split")])
+def test_planner_tables_1d_against_oracle(lib, shape, r, t, dtype):
+    """1D plans (patches of 128 consecutive outputs): A' is the single local staircase of
+    Sec. 3.1 (r1 = 128), the pairs are Algorithm 1's on one block, the LUT reads column c of
+    the patch window at tile word c + G - R, and the decompressed A'' un-permutes to A'."""
+    w = inputs.stencil_weights(shape, 1, r, "random", seed=7)
+    plan = binding.Plan(w, (100000,), dtype=dtype, bc="periodic", fusion_depth=t, shape=shape)
+    info = plan.info()
+    tb = plan.tables()
+    k = 2 * t * r + 1
+    np.testing.assert_allclose(tb["fused_w"], _composed_1d(w, t), rtol=1e-13, atol=1e-16)
+    wf32 = tb["fused_w"].astype(np.float32).astype(np.float64)
+    A = morph.local_staircase(wf32, 128)
+    assert info.r1 == 128 and info.kprime == A.shape[1] == k + 127
+    _, _, M = morph.hierarchical_matching(A.shape[1], A.shape[1], k)
+    alg = [v for pr in M for v in pr]
+    order = tb["order"]
+
+    def pairset(o):
+        return sorted(tuple(sorted((int(o[2 * i]), int(o[2 * i + 1])))) for i in range(len(o) // 2)
+                      if not (o[2 * i] == ZERO and o[2 * i + 1] == ZERO))
+    assert info.pairing == 0 and pairset(order) == pairset(alg)
+    assert info.kpad == len(order) == (len(alg) + 31) // 32 * 32
+    G, R = info.ghost, t * r
+    real = order != ZERO
+    np.testing.assert_array_equal(tb["lut"][real], order[real] + G - R)
+    dense = morph.decompress_2_4(tb["a_hi"].astype(np.float64) + tb["a_lo"], tb["a_idx"])
+    assert morph.satisfies_2_4(dense)
+    Ap = morph.apply_permutation(A, list(order))
+    if dtype == "bf16_split" and info.mma_terms == 4:
+        np.testing.assert_array_equal(dense, Ap)  # three BF16 pieces: exact
+    else:
+        assert np.max(np.abs(dense - Ap)) <= 2.0 ** -15 * np.max(np.abs(A))
+
+
+def _composed_1d(w, t):
+    """t-step 1D kernel read off the oracle: one impulse, t steps."""
+    import oracle
+    r = (w.shape[0] - 1) // 2
+    R = t * r
+    n = 4 * R + 3
+    u = np.zeros(n)
+    u[n // 2] = 1.0
+    out = oracle.run(u, w.astype(np.float64), "periodic", t)
+    return out[n // 2 - R:n // 2 + R + 1][::-1]
+
+
 def _oracle_order_3d(wf, k, r1, r2, r3):
     """The 3D reading: nested staircase A' and Algorithm 1 applied level by level."""
     A = morph.crushed_weights_3d(wf, r1, r2, r3)
