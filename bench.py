@@ -269,7 +269,8 @@ def main():
     ap.add_argument("--ncu-case", default=None,
                     help="profiling case for ncu: '<precision>:<side>' runs a few single sweeps of Box-2D9P "
                          "on a side x side periodic grid and exits (no JSON line)")
-    ap.add_argument("--suite", action="store_true", help="configs C1, C3, C4a/b (one JSON line each) and exit")
+    ap.add_argument("--suite", action="store_true",
+                    help="configs C1, C3, C4a/b and Heat-1D / 1D5P (one JSON line each) and exit")
     ap.add_argument("--batch", action="store_true", help="config C4c (64 grids in one CUDA graph) and exit")
     ap.add_argument("--serve", action="store_true", help="config C5 (Poisson-arrival job server) and exit")
     ap.add_argument("--ablation", action="store_true",
@@ -543,7 +544,7 @@ def suite_mode():
         elif cfg["ndim"] == 3:
             dtypes = ("fp16", "bf16", "fp16_split", "bf16_split")
         elif cfg["ndim"] == 1:
-            dtypes = ("bf16", "bf16_split")
+            dtypes = ("fp16", "bf16", "fp16_split", "bf16_split")
         else:
             dtypes = ("bf16", "bf16_split")
         full_ref = oracle.run(u, w, bc, T) if name == "heat2d_512" else None
