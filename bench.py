@@ -164,6 +164,21 @@ def cpu_oracle_sample(target_s: float = 15.0):
                       f"steps ({dt:.1f} s)"}
 
 
+def replica_throughput(local_ms_total, runs, points_per_run, dist=None, device="cpu"):
+    """Whole-job GStencil/s of N independent replicas (no data-path collective): every rank
+    timed `runs` runs of `points_per_run` point-steps; the slowest rank's total time counts
+    (max over ranks).  Returns (GStencil/s, that time in ms)."""
+    import torch
+    tot = float(local_ms_total)
+    world = 1
+    if dist is not None:
+        world = dist.get_world_size()
+        t = torch.tensor([tot], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    return world * runs * points_per_run / (tot / 1e3) / 1e9, tot
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle as it stands, on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -379,12 +394,7 @@ def main():
     clock_info["window"] = "fusion-depth search + warm-up + timed runs, 20 ms period"
     if dist is not None:
         dist.barrier()
-    tot = sum(run_ms)
-    if dist is not None:
-        tt = torch.tensor([tot], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot = float(tt.item())
-    value = world * args.steps * pts / (tot / 1e3) / 1e9
+    value, tot = replica_throughput(sum(run_ms), args.steps, pts, dist, "cuda")
     status = binding.device_status()
 
     # per-kernel device time of the sweeps (events around each launch)
@@ -416,7 +426,7 @@ def main():
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             e2e_ms.append(dt * 1e3)
-    e2e_val = world * len(e2e_ms) * pts / (sum(e2e_ms) / 1e3) / 1e9
+    e2e_val, _ = replica_throughput(sum(e2e_ms), len(e2e_ms), pts, dist, "cuda")
 
     # variants: single-word BF16 and the plain FP32 CUDA-core direct stencil
     t1, _, plan1 = autotune("bf16")
