@@ -136,9 +136,11 @@ sparstencil_status sparstencil_plan_set_dense_ablation(sparstencil_plan_t plan, 
 sparstencil_status sparstencil_run(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
                                    cudaStream_t stream);
 
-/* Same as sparstencil_run with HOST grids: copies in (host) to the device, runs, and copies
- * the result back to out (host), all on `stream`.  Synchronises the stream before
- * returning.  Page-locked host memory makes the copies asynchronous to the CPU. */
+/* Same as sparstencil_run with HOST grids: brings in (host) to the device, runs, and copies
+ * the result back to out (host), all on `stream`.  Page-locked input that the device can
+ * address (cudaHostAlloc / cudaHostRegister) is read directly by the copy-in kernel; other
+ * input is first copied to a device staging grid.  Synchronises the stream before
+ * returning. */
 sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in_host, float* out_host,
                                         int64_t timesteps, cudaStream_t stream);
 

@@ -911,8 +911,19 @@ sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in
       return fail(SPST_ERR_NOMEM, "staging allocation failed");
     }
   }
-  SPST_CUDA(cudaMemcpyAsync(plan->stage_in, in_host, bytes, cudaMemcpyHostToDevice, stream), "H2D");
-  s = run_sweeps(plan, plan->stage_in, plan->stage_out, timesteps, stream);
+  // Page-locked host memory that the device can address (cudaHostAlloc / cudaHostRegister)
+  // is read by the copy-in kernel itself, which saves the staging copy; other host memory
+  // is copied to the device first.
+  const float* src = plan->stage_in;
+  cudaPointerAttributes at;
+  if (timesteps > 0 && cudaPointerGetAttributes(&at, in_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer)
+    src = (const float*)at.devicePointer;
+  else
+    cudaGetLastError();
+  if (src == plan->stage_in)
+    SPST_CUDA(cudaMemcpyAsync(plan->stage_in, in_host, bytes, cudaMemcpyHostToDevice, stream), "H2D");
+  s = run_sweeps(plan, src, plan->stage_out, timesteps, stream);
   if (s != SPST_OK) return s;
   SPST_CUDA(cudaMemcpyAsync(out_host, plan->stage_out, bytes, cudaMemcpyDeviceToHost, stream), "D2H");
   SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
