@@ -572,6 +572,16 @@ def suite_mode():
                 line[f"{dt}_low_accumulator"] = plan.info().low_accumulator
             if sample is not None:
                 line[f"{dt}_rel_l2_sampled_vs_oracle"] = sampled_l2(y)
+            if name == "heat2d_512":
+                # latency-bound: also the run replayed from a CUDA graph (no host work per run)
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    plan.run(x, y, T)
+                gms, _ = _time_runs(graph.replay, 5, 2, flush)
+                line[f"{dt}_graph_us_per_run"] = gms * 1e3
+                line[f"{dt}_graph_gstencil_s"] = pts / gms / 1e6
+                line[f"{dt}_us_per_run"] = ms * 1e3
+                graph.replay()
             if full_ref is not None:
                 l2, linf = oracle.rel_errors(y.cpu().numpy().astype(np.float64), full_ref)
                 line[f"{dt}_rel_l2_vs_oracle"] = l2

@@ -132,7 +132,10 @@ sparstencil_status sparstencil_plan_set_dense_ablation(sparstencil_plan_t plan, 
  *   timesteps = 0 copies in to out.
  * Uses the plan's workspace (bound, or allocated on first use: SPST_ERR_NOMEM on failure).
  * Asynchronous: enqueues the sweeps (ceil(timesteps / t) kernels plus one copy-in) and
- * returns.  Calls on one plan must not overlap on the GPU (they share the workspace). */
+ * returns.  Calls on one plan must not overlap on the GPU (they share the workspace).
+ * A run may be captured into a CUDA graph (stream capture on `stream`) once the plan has run
+ * once with the same timesteps (workspace and tables on the device, fusion depth chosen);
+ * inside a capture the sweeps launch in plain stream order. */
 sparstencil_status sparstencil_run(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
                                    cudaStream_t stream);
 

@@ -77,6 +77,14 @@ struct DeviceTables {
 
 bool is_split(sparstencil_dtype d) { return d == SPST_FP16_SPLIT || d == SPST_BF16_SPLIT; }
 
+// Programmatic dependent launch between sweeps: on, except while a CUDA graph is captured
+// (this thread's setting, mirrored here so that a run can restore it)
+thread_local bool t_pdl_on = true;
+void set_programmatic_launch(bool on) {
+  t_pdl_on = on;
+  spst::sweep2d_set_programmatic_launch(on);
+}
+
 // TMEM columns: accumulators (128 each) + A'' pieces + metadata (8-column pairs of chunks),
 // or for the dense ablation the uncompressed A' pieces (K/2 columns each) and no metadata.
 // Returns the tile buffers that fit in the 512 columns: two accumulators when they fit, else
@@ -545,6 +553,16 @@ sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out,
     s = ensure_device_tables(p, sweeps[i], *tabs[i], &dtabs[i]);
     if (s != SPST_OK) return s;
   }
+  // a run that the caller captures into a CUDA graph launches in plain stream order (the
+  // graph's edges order its kernels)
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  SPST_CUDA(cudaStreamIsCapturing(stream, &capture), "stream capture status");
+  const bool pdl_before = t_pdl_on;
+  if (capture != cudaStreamCaptureStatusNone) set_programmatic_launch(false);
+  struct RestorePdl {
+    bool on;
+    ~RestorePdl() { set_programmatic_launch(on); }
+  } restore_pdl{pdl_before};
   if (timer && (s = timer->record(stream)) != SPST_OK) return s;
   SPST_CUDA(copy_in(p, in, p->pad(0), T, stream, p->maxabs), "pad copy");
   if (timer && (s = timer->record(stream)) != SPST_OK) return s;
@@ -968,7 +986,7 @@ sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const 
   cudaGraphExec_t exec = nullptr;
   sparstencil_status s = SPST_OK;
   auto cleanup = [&]() {
-    spst::sweep2d_set_programmatic_launch(true);
+    set_programmatic_launch(true);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (auto e : ev)
@@ -991,7 +1009,7 @@ sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const 
     cleanup();
     return s;
   }
-  spst::sweep2d_set_programmatic_launch(false);  // plain stream order inside the graph
+  set_programmatic_launch(false);  // plain stream order inside the graph
   if (cuda_ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture")) {
     cuda_ok(cudaEventRecord(ev[nb], cap), "fork event");
     for (int b = 0; b < nb && s == SPST_OK; b++) cuda_ok(cudaStreamWaitEvent(br[b], ev[nb], 0), "fork wait");

@@ -226,6 +226,29 @@ def test_bounded_wait_reports_timeout(torch_cuda):
     assert binding.device_status() == 0
 
 
+def test_run_captured_in_a_cuda_graph(torch_cuda):
+    """A run captured into a CUDA graph (after one plain run) replays to the same result,
+    bit for bit, and leaves later plain runs unchanged."""
+    torch = torch_cuda
+    w = inputs.stencil_weights("star", 2, 1, "heat", seed=1)
+    u = inputs.uniform01(3, (512, 512))
+    plan = binding.Plan(w, u.shape, dtype="fp16", bc="dirichlet", fusion_depth=0, shape="star")
+    x = torch.from_numpy(u).cuda()
+    y0, y1, y2 = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+    plan.run(x, y0, 8)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.run(x, y1, 8)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    plan.run(x, y2, 8)
+    torch.cuda.synchronize()
+    assert binding.device_status() == 0
+    assert torch.equal(y1, y0) and torch.equal(y2, y0)
+
+
 def test_batch_graph_equals_individual_runs(torch_cuda):
     """sparstencil_run_batch (one CUDA graph, jobs side by side) gives each job exactly the
     result of sparstencil_run on its own: mixed sizes, stencils, precisions, boundaries and
