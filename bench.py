@@ -230,6 +230,35 @@ def ncu_case(spec: str, t: int):
     assert binding.device_status() == 0
 
 
+def ncu_kernels_case():
+    """Profiling case covering every kernel of the library once or twice, each on inputs larger
+    than L2 where the kernel streams a grid: the 3D sweep (Heat-3D 384^3, FP16, with its copy-in
+    and, periodic, its ghost refresh), the 1D sweep (Heat-1D 2^26, BF16 split, t = 8), the
+    Dirichlet band of a fused 2D sweep (Heat-2D 8192^2, t = 3), the FP32 direct kernels (1D,
+    2D radius 1 and 3, 3D radius 1) and the FP64 error norms."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_22969_gb300 import binding, inputs
+    cases = [("star", 3, 1, "random", (384, 384, 384), "fp16", "periodic", 1, 1),
+             ("star", 1, 1, "heat", (1 << 26,), "bf16_split", "periodic", 8, 8),
+             ("star", 2, 1, "heat", (8192, 8192), "bf16", "dirichlet", 3, 3)]
+    for shape, nd, r, recipe, dims, dt, bc, t, steps in cases:
+        w = inputs.stencil_weights(shape, nd, r, recipe, seed=1)
+        x = torch.from_numpy(inputs.uniform01(1, dims)).cuda()
+        y = torch.empty_like(x)
+        plan = binding.Plan(w, dims, dtype=dt, bc=bc, fusion_depth=t, shape=shape)
+        plan.run(x, y, steps)
+        binding.direct_run(w, x, y, torch.empty_like(x), 1, bc=bc)
+        if len(dims) == 2:
+            w3 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=1)
+            binding.direct_run(w3, x, y, torch.empty_like(x), 1, bc=bc)
+        binding.error_norms(y, x)
+        del x, y
+        torch.cuda.synchronize()
+    assert binding.device_status() == 0
+
+
 def trace_case():
     """Prints the CTA-0 timeline (microseconds from the first TMA issue) of one sweep for
     each precision and fused depth of the workload.  Needs a library built with
@@ -288,6 +317,8 @@ def main():
                     help="configs C1, C3, C4a/b and Heat-1D / 1D5P (one JSON line each) and exit")
     ap.add_argument("--batch", action="store_true", help="config C4c (64 grids in one CUDA graph) and exit")
     ap.add_argument("--serve", action="store_true", help="config C5 (Poisson-arrival job server) and exit")
+    ap.add_argument("--ncu-kernels", action="store_true",
+                    help="profiling case: one launch or two of every kernel of the library, then exit")
     ap.add_argument("--ablation", action="store_true",
                     help="dense versus sparse tensor-core MMAs on Box-2D49P at several sizes and exit")
     args = ap.parse_args()
@@ -299,6 +330,8 @@ def main():
         return serve_mode()
     if args.ablation:
         return ablation_mode()
+    if args.ncu_kernels:
+        return ncu_kernels_case()
     if args.impl == "reference":
         return run_reference(args)
     if args.ncu_case:

@@ -25,50 +25,89 @@ __device__ __forceinline__ void fold_maxabs(unsigned* maxabs, float m) {
   if ((threadIdx.x & 31) == 0) atomicMax(maxabs, b);
 }
 
-__global__ void pad_copy2d_kernel(const float* __restrict__ in, float* __restrict__ out, int H, int W, int G,
-                                  int64_t Wp, int periodic, unsigned* maxabs) {
-  const int64_t Hp = (int64_t)H + 2 * G;
-  const int64_t total = Hp * Wp;
-  float m = 0.f;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < total; i0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = i0 + threadIdx.x;
-    if (i >= total) continue;
-    const int64_t yp = i / Wp, xp = i % Wp;
-    int64_t y = yp - G, x = xp - G;
-    float v = 0.f;
-    if (xp < (int64_t)W + 2 * G) {
-      if (periodic) {
-        y = y < 0 ? y + H : (y >= H ? y - H : y);
-        x = x < 0 ? x + W : (x >= W ? x - W : x);
-        v = in[y * W + x];
-      } else if (y >= 0 && y < H && x >= 0 && x < W) {
-        v = in[y * W + x];
+// One padded row dst[0, Wp) from source row src[0, W) with G ghost cells each side (wrapped
+// images, or zeros when not periodic or when the row itself lies outside: inside = false),
+// zeros past W + 2G; the block's threads take four elements each per step (independent
+// loads in flight), and *m collects max |value|.
+__device__ __forceinline__ void copy_padded_row(const float* __restrict__ src, float* __restrict__ dst, int64_t W,
+                                                int G, int64_t Wp, int periodic, bool inside, float* m) {
+  const int64_t step = 4 * (int64_t)blockDim.x;
+  for (int64_t x0 = threadIdx.x; x0 < Wp; x0 += step) {
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int64_t xp = x0 + k * (int64_t)blockDim.x;
+      int64_t x = xp - G;
+      v[k] = 0.f;
+      if (xp < W + 2 * G) {
+        if (periodic) {
+          x = x < 0 ? x + W : (x >= W ? x - W : x);
+          v[k] = src[x];
+        } else if (inside && x >= 0 && x < W) {
+          v[k] = src[x];
+        }
       }
     }
-    out[i] = v;
-    m = fmaxf(m, fabsf(v));
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int64_t xp = x0 + k * (int64_t)blockDim.x;
+      if (xp < Wp) {
+        dst[xp] = v[k];
+        *m = fmaxf(*m, fabsf(v[k]));
+      }
+    }
+  }
+}
+
+__global__ void pad_copy2d_kernel(const float* __restrict__ in, float* __restrict__ out, int H, int W, int G,
+                                  int64_t Wp, int periodic, unsigned* maxabs) {
+  // a CTA per padded row (grid-stride over rows), its threads along x
+  const int64_t Hp = (int64_t)H + 2 * G;
+  float m = 0.f;
+  for (int64_t yp = blockIdx.x; yp < Hp; yp += gridDim.x) {
+    int64_t y = yp - G;
+    bool inside = true;
+    if (periodic)
+      y = y < 0 ? y + H : (y >= H ? y - H : y);
+    else
+      inside = y >= 0 && y < H;
+    const float* src = in + (inside ? y * W : 0);
+    float* dst = out + yp * Wp;
+    copy_padded_row(src, dst, W, G, Wp, periodic, inside, &m);
   }
   fold_maxabs(maxabs, m);
 }
 
 __global__ void pad_copy1d_kernel(const float* __restrict__ in, float* __restrict__ out, int64_t W, int G,
                                   int64_t Wp, int periodic, unsigned* maxabs) {
+  // block b copies segment [b * 1024, (b + 1) * 1024) of the padded line (grid-stride)
   float m = 0.f;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < Wp; i0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t xp = i0 + threadIdx.x;
-    if (xp >= Wp) continue;
-    int64_t x = xp - G;
-    float v = 0.f;
-    if (xp < W + 2 * G) {
-      if (periodic) {
-        x = x < 0 ? x + W : (x >= W ? x - W : x);
-        v = in[x];
-      } else if (x >= 0 && x < W) {
-        v = in[x];
+  constexpr int64_t kSeg = 1024;
+  for (int64_t s0 = (int64_t)blockIdx.x * kSeg; s0 < Wp; s0 += (int64_t)gridDim.x * kSeg) {
+    const int64_t n = Wp - s0 < kSeg ? Wp - s0 : kSeg;
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int64_t xp = s0 + threadIdx.x + k * (int64_t)blockDim.x;
+      int64_t x = xp - G;
+      v[k] = 0.f;
+      if (xp < s0 + n && xp < W + 2 * G) {
+        if (periodic) {
+          x = x < 0 ? x + W : (x >= W ? x - W : x);
+          v[k] = in[x];
+        } else if (x >= 0 && x < W) {
+          v[k] = in[x];
+        }
       }
     }
-    out[xp] = v;
-    m = fmaxf(m, fabsf(v));
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int64_t xp = s0 + threadIdx.x + k * (int64_t)blockDim.x;
+      if (xp < s0 + n) {
+        out[xp] = v[k];
+        m = fmaxf(m, fabsf(v[k]));
+      }
+    }
   }
   fold_maxabs(maxabs, m);
 }
@@ -272,15 +311,19 @@ __global__ void direct3d_kernel(const __grid_constant__ DirectParams p, const fl
 // ---------------------------------------------------------------------------------------
 __global__ void norms_kernel(const float* __restrict__ x, const float* __restrict__ ref, int64_t n,
                              double* __restrict__ acc) {
-  double s0 = 0.0, s1 = 0.0, m0 = 0.0, m1 = 0.0;
+  // the difference and the maxima in FP32 (x - ref rounds once, 2^-24 relative), the sums of
+  // squares in FP64; FP64 throughput, not memory, bounds a kernel that does more in FP64
+  double s0 = 0.0, s1 = 0.0;
+  float m0f = 0.f, m1f = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double a = (double)x[i], b = (double)ref[i];
-    const double d = a - b;
-    s0 += d * d;
-    s1 += b * b;
-    m0 = fmax(m0, fabs(d));
-    m1 = fmax(m1, fabs(b));
+    const float a = x[i], b = ref[i];
+    const float d = a - b;
+    s0 = fma((double)d, (double)d, s0);
+    s1 = fma((double)b, (double)b, s1);
+    m0f = fmaxf(m0f, fabsf(d));
+    m1f = fmaxf(m1f, fabsf(b));
   }
+  double m0 = m0f, m1 = m1f;
   for (int o = 16; o > 0; o >>= 1) {
     s0 += __shfl_down_sync(0xffffffffu, s0, o);
     s1 += __shfl_down_sync(0xffffffffu, s1, o);
@@ -370,27 +413,23 @@ __global__ void band2d_kernel(const BandParams p) {
 // ---------------------------------------------------------------------------------------
 __global__ void pad_copy3d_kernel(const float* __restrict__ in, float* __restrict__ out, int D, int H, int W, int G,
                                   int64_t Wp, int periodic, unsigned* maxabs) {
+  // a CTA per padded row (grid-stride over rows), its threads along x: the row's source row
+  // is found once, and loads and stores are contiguous
   const int64_t Hp = (int64_t)H + 2 * G, Dp = (int64_t)D + 2 * G;
-  const int64_t total = Dp * Hp * Wp;
+  const int64_t rows = Dp * Hp;
   float m = 0.f;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < total; i0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = i0 + threadIdx.x;
-    if (i >= total) continue;
-    const int64_t xp = i % Wp, yp = (i / Wp) % Hp, zp = i / (Wp * Hp);
-    int64_t z = zp - G, y = yp - G, x = xp - G;
-    float v = 0.f;
-    if (xp < (int64_t)W + 2 * G) {
-      if (periodic) {
-        z = z < 0 ? z + D : (z >= D ? z - D : z);
-        y = y < 0 ? y + H : (y >= H ? y - H : y);
-        x = x < 0 ? x + W : (x >= W ? x - W : x);
-        v = in[(z * H + y) * W + x];
-      } else if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W) {
-        v = in[(z * H + y) * W + x];
-      }
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    int64_t z = row / Hp - G, y = row % Hp - G;
+    bool inside = true;
+    if (periodic) {
+      z = z < 0 ? z + D : (z >= D ? z - D : z);
+      y = y < 0 ? y + H : (y >= H ? y - H : y);
+    } else {
+      inside = z >= 0 && z < D && y >= 0 && y < H;
     }
-    out[i] = v;
-    m = fmaxf(m, fabsf(v));
+    const float* src = in + (inside ? (z * H + y) * W : 0);
+    float* dst = out + row * Wp;
+    copy_padded_row(src, dst, W, G, Wp, periodic, inside, &m);
   }
   fold_maxabs(maxabs, m);
 }
@@ -423,10 +462,9 @@ __global__ void ghost_refresh3d_kernel(float* __restrict__ g3, int D, int H, int
 
 cudaError_t launch_pad_copy3d(const float* in, float* padded, int D, int H, int W, int G, int64_t Wp, int periodic,
                               unsigned* maxabs, cudaStream_t stream) {
-  const int64_t total = ((int64_t)D + 2 * G) * ((int64_t)H + 2 * G) * Wp;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  pad_copy3d_kernel<<<(unsigned)blocks, 256, 0, stream>>>(in, padded, D, H, W, G, Wp, periodic, maxabs);
+  const int64_t rows = ((int64_t)D + 2 * G) * ((int64_t)H + 2 * G);
+  const int64_t blocks = rows < 152 * 32 ? rows : 152 * 32;
+  pad_copy3d_kernel<<<(unsigned)blocks, 128, 0, stream>>>(in, padded, D, H, W, G, Wp, periodic, maxabs);
   return cudaGetLastError();
 }
 
@@ -439,7 +477,7 @@ cudaError_t launch_ghost_refresh3d(float* padded, int D, int H, int W, int G, in
 
 cudaError_t launch_pad_copy1d(const float* in, float* out, int64_t W, int G, int64_t Wp, int periodic,
                               unsigned* maxabs, cudaStream_t stream) {
-  int64_t blocks = (Wp + 255) / 256;
+  int64_t blocks = (Wp + 1023) / 1024;
   if (blocks > 152 * 16) blocks = 152 * 16;
   pad_copy1d_kernel<<<(unsigned)blocks, 256, 0, stream>>>(in, out, W, G, Wp, periodic, maxabs);
   return cudaGetLastError();
@@ -452,9 +490,8 @@ cudaError_t launch_ghost_refresh1d(float* line, int64_t W, int G, cudaStream_t s
 
 cudaError_t launch_pad_copy2d(const float* in, float* padded, int H, int W, int G, int64_t Wp, int periodic,
                               unsigned* maxabs, cudaStream_t stream) {
-  const int64_t total = ((int64_t)H + 2 * G) * Wp;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const int64_t rows = (int64_t)H + 2 * G;
+  const int64_t blocks = rows < 152 * 32 ? rows : 152 * 32;
   pad_copy2d_kernel<<<(unsigned)blocks, 256, 0, stream>>>(in, padded, H, W, G, Wp, periodic, maxabs);
   return cudaGetLastError();
 }
