@@ -223,19 +223,31 @@ __global__ void __launch_bounds__(256) direct3d_r1_kernel(const __grid_constant_
                                                           const float* __restrict__ in, float* __restrict__ out) {
   constexpr int TW = E3X + 2, TH = E3Y + 2, TD = E3Z + 2;
   __shared__ float tile[TD * TH * TW];
+  __shared__ int64_t row_off[TD * TH];  // source offset of tile row (z, y), -1: outside (zeros)
   const int64_t D = p.D, H = p.H, W = p.W;
   const int64_t x0 = (int64_t)blockIdx.x * E3X, y0 = (int64_t)blockIdx.y * E3Y, z0 = (int64_t)blockIdx.z * E3Z;
-  for (int i = threadIdx.x; i < TW * TH * TD; i += blockDim.x) {
-    const int tz = i / (TW * TH), ty = (i / TW) % TH, tx = i % TW;
-    int64_t z = z0 + tz - 1, y = y0 + ty - 1, x = x0 + tx - 1;
-    float v = 0.f;
+  // the boundary rule along z and y is applied once per tile row, along x per element
+  for (int r = threadIdx.x; r < TD * TH; r += blockDim.x) {
+    int64_t z = z0 + r / TH - 1, y = y0 + r % TH - 1;
     if (p.periodic) {
       z = z < 0 ? z + D : (z >= D ? z - D : z);
       y = y < 0 ? y + H : (y >= H ? y - H : y);
+      row_off[r] = (z * H + y) * W;
+    } else {
+      row_off[r] = (z >= 0 && z < D && y >= 0 && y < H) ? (z * H + y) * W : -1;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < TW * TH * TD; i += blockDim.x) {
+    const int r = i / TW, tx = i - r * TW;
+    int64_t x = x0 + tx - 1;
+    const int64_t off = row_off[r];
+    float v = 0.f;
+    if (p.periodic) {
       x = x < 0 ? x + W : (x >= W ? x - W : x);
-      v = in[(z * H + y) * W + x];
-    } else if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W) {
-      v = in[(z * H + y) * W + x];
+      v = in[off + x];
+    } else if (off >= 0 && x >= 0 && x < W) {
+      v = in[off + x];
     }
     tile[i] = v;
   }
