@@ -149,6 +149,38 @@ struct sparstencil_plan_s {
 
 namespace {
 
+// Process-wide cache of planner tables.  The tables depend on the composed weights, the
+// fused radius, the word, the piece count and the tile geometry (pitch, box height, ghost
+// width), not on the grid's extents, so plans of one stencil on grids of different sizes
+// (a job server's usual load) share them.  Bounded: cleared when it holds kTableCacheMax sets.
+constexpr size_t kTableCacheMax = 64;
+std::mutex g_table_cache_mu;
+std::map<std::string, SweepTables> g_table_cache;
+
+std::string tables_cached(const std::vector<double>& wf, int R, const PlanGeometry& geo, spst::Word word, int pieces,
+                          SweepTables* out) {
+  std::string key;
+  auto put = [&](const void* q, size_t n) { key.append((const char*)q, n); };
+  const int ints[6] = {R, geo.ndim, geo.P, geo.box_h, geo.G, pieces};
+  put(ints, sizeof(ints));
+  put(&word, sizeof(word));
+  put(wf.data(), wf.size() * sizeof(double));
+  {
+    std::lock_guard<std::mutex> lock(g_table_cache_mu);
+    auto it = g_table_cache.find(key);
+    if (it != g_table_cache.end()) {
+      *out = it->second;
+      return "";
+    }
+  }
+  std::string err = spst::build_sweep_tables_2d(wf, R, geo, word, pieces, true, out);
+  if (!err.empty()) return err;
+  std::lock_guard<std::mutex> lock(g_table_cache_mu);
+  if (g_table_cache.size() >= kTableCacheMax) g_table_cache.clear();
+  g_table_cache.emplace(std::move(key), *out);
+  return "";
+}
+
 std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
   std::vector<double> wf = spst::compose_weights(p->w64, p->ndim, p->radius, depth);
   // Weight pieces: single-word operands use two 16-bit pieces.  BF16 split operands use three
@@ -164,13 +196,13 @@ std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
   // ablation's uncompressed A' takes twice the columns; in every case two pieces replace three
   // when they leave room for more tile buffers.
   const int pieces = (is_split(p->dtype) && word_of(p->dtype) == spst::Word::BF16) ? 3 : 2;
-  std::string err = spst::build_sweep_tables_2d(wf, depth * p->radius, p->geo, word_of(p->dtype), pieces, true, out);
+  std::string err = tables_cached(wf, depth * p->radius, p->geo, word_of(p->dtype), pieces, out);
   if (!err.empty()) return err;
   const int buffers3 = tmem_accumulators(*out, p->lo_acc, p->dense);
   const bool retry = buffers3 == 0 || (!p->lo_acc && depth >= 2 && buffers3 < 2);
   if (pieces == 3 && retry) {
     SweepTables two;
-    err = spst::build_sweep_tables_2d(wf, depth * p->radius, p->geo, word_of(p->dtype), 2, true, &two);
+    err = tables_cached(wf, depth * p->radius, p->geo, word_of(p->dtype), 2, &two);
     if (!err.empty()) return err;
     if (tmem_accumulators(two, p->lo_acc, p->dense) > tmem_accumulators(*out, p->lo_acc, p->dense))
       *out = std::move(two);

@@ -328,6 +328,21 @@ def test_dense_ablation_setting(lib):
     assert p71.info().dense_ablation == 1 and p71.info().mma_terms == 3
 
 
+def test_plans_of_one_stencil_share_tables(lib):
+    """Planner tables depend on the stencil and the tile geometry, not on the grid's extents:
+    plans of one stencil on grids of different sizes get the same tables (from the
+    process-wide cache), and a stencil with other weights gets its own."""
+    w = inputs.stencil_weights("star", 3, 1, "random", seed=21)
+    a = binding.Plan(w, (40, 36, 72), dtype="bf16_split", fusion_depth=1, shape="star").tables()
+    b = binding.Plan(w, (64, 48, 200), dtype="bf16_split", fusion_depth=1, shape="star").tables()
+    for k in ("order", "lut", "a_hi", "a_lo", "a_idx"):
+        np.testing.assert_array_equal(a[k], b[k])
+    w2 = w.copy()
+    w2[1, 1, 1] *= 0.5
+    c = binding.Plan(w2, (40, 36, 72), dtype="bf16_split", fusion_depth=1, shape="star").tables()
+    assert not np.array_equal(a["a_hi"] + a["a_lo"], c["a_hi"] + c["a_lo"])
+
+
 def test_cost_model_entry_point(lib):
     """sparstencil_cost_model (Eq. 6-11): with a fast tensor pipe the HBM term binds and the
     time per step falls as 1/t; with a slow one the compute term binds and grows with the
