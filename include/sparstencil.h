@@ -250,6 +250,9 @@ sparstencil_status sparstencil_error_norms(const float* x, const float* ref, int
  * (SPST_ERR_TIMEOUT, SPST_ERR_DEVICE_CHECK). */
 sparstencil_status sparstencil_device_status(cudaStream_t stream);
 
+/* The same as sparstencil_device_status (the name the problem statement's interface uses). */
+sparstencil_status sparstencil_stream_status(cudaStream_t stream);
+
 /* Sets the bound (nanoseconds) of every device-side wait; 0 restores the default (2 s).
  * Host only; applies to launches made after the call. */
 sparstencil_status sparstencil_set_wait_limit_ns(uint64_t ns);

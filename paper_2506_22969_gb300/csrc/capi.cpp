@@ -1226,4 +1226,6 @@ sparstencil_status sparstencil_device_status(cudaStream_t stream) {
   return SPST_OK;
 }
 
+sparstencil_status sparstencil_stream_status(cudaStream_t stream) { return sparstencil_device_status(stream); }
+
 }  // extern "C"
