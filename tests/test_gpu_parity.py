@@ -448,3 +448,33 @@ def test_full_size_1d_sampled(torch_cuda, oracle_mod, name):
     ref = np.array([oracle_mod.point(u64, w, cfg["bc"], cfg["steps"], p) for p in pts])
     vals = np.array([got[p] for p in pts])
     assert np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2)) <= 1e-5, plan.info().fusion_depth
+
+
+def _custom(mask, seed):
+    rng = np.random.default_rng(seed)
+    w = np.where(mask, 0.05 + 0.95 * rng.random(mask.shape), 0.0)
+    return (w / w.sum()).astype(np.float32)
+
+
+@pytest.mark.parametrize("name,dims,steps,bc,dtype,t", [
+    ("upwind2d", (300, 260), 12, "periodic", "bf16_split", 2),
+    ("upwind2d", (256, 200), 7, "dirichlet", "fp16", 1),
+    ("knight2d", (260, 300), 9, "periodic", "bf16", 1),
+    ("forward3d", (40, 36, 72), 6, "periodic", "fp16_split", 1),
+])
+def test_custom_mask_matches_oracle(torch_cuda, oracle_mod, name, dims, steps, bc, dtype, t):
+    """Arbitrary (asymmetric, non-staircase) masks through the CUSTOM shape: the sparse path
+    matches the oracle at the dtype's tolerance."""
+    mask = {"upwind2d": np.array([[1, 1, 0], [1, 1, 0], [0, 0, 0]], bool),
+            "knight2d": np.array([[0, 1, 0, 1, 0], [1, 0, 0, 0, 1], [0, 0, 1, 0, 0], [1, 0, 0, 0, 1],
+                                  [0, 1, 0, 1, 0]], bool)}.get(name)
+    if mask is None:
+        mask = np.zeros((3, 3, 3), bool)
+        mask[1, 1, 1] = mask[2, 1, 1] = mask[1, 2, 1] = mask[1, 1, 2] = True
+    w = _custom(mask, 32)
+    u = inputs.uniform01(10, dims)
+    ref = oracle_mod.run(u, w, bc, steps)
+    got, plan = _run_sparse(torch_cuda, u, w, steps, dtype, bc, t, "custom")
+    l2, linf = oracle_mod.rel_errors(got, ref)
+    assert np.all(np.isfinite(got))
+    assert l2 <= TOL[dtype], (l2, linf, plan.info().pairing)

@@ -328,6 +328,57 @@ def test_dense_ablation_setting(lib):
     assert p71.info().dense_ablation == 1 and p71.info().mma_terms == 3
 
 
+def _custom_weights(mask, seed):
+    """Positive weights on an arbitrary mask (offset-indexed cube), normalised to sum 1."""
+    rng = np.random.default_rng(seed)
+    w = np.where(mask, 0.05 + 0.95 * rng.random(mask.shape), 0.0)
+    return (w / w.sum()).astype(np.float32)
+
+
+CUSTOM_MASKS = {
+    # 2D upwind corner: centre, west, north, north-west (asymmetric)
+    "upwind2d": np.array([[1, 1, 0], [1, 1, 0], [0, 0, 0]], bool),
+    # 2D knight moves plus centre, radius 2
+    "knight2d": np.array([[0, 1, 0, 1, 0], [1, 0, 0, 0, 1], [0, 0, 1, 0, 0], [1, 0, 0, 0, 1], [0, 1, 0, 1, 0]], bool),
+    # 3D: centre and the three "forward" neighbours
+    "forward3d": np.zeros((3, 3, 3), bool),
+}
+CUSTOM_MASKS["forward3d"][1, 1, 1] = CUSTOM_MASKS["forward3d"][2, 1, 1] = True
+CUSTOM_MASKS["forward3d"][1, 2, 1] = CUSTOM_MASKS["forward3d"][1, 1, 2] = True
+
+
+@pytest.mark.parametrize("name,t", [("upwind2d", 1), ("upwind2d", 2), ("knight2d", 1), ("forward3d", 1)])
+def test_custom_mask_tables(lib, name, t):
+    """CUSTOM shapes: any support inside the cube.  The tables hold the oracle's A' after
+    un-permutation, every pair holds at most one nonzero per row, and with the maximum-matching
+    pairing the zero columns equal the optimum of Problem 1 on the support."""
+    mask = CUSTOM_MASKS[name]
+    w = _custom_weights(mask, 31)
+    nd = mask.ndim
+    dims = (300, 260) if nd == 2 else (40, 36, 72)
+    plan = binding.Plan(w, dims, dtype="bf16_split", bc="periodic", fusion_depth=t, shape="custom")
+    info = plan.info()
+    tb = plan.tables()
+    wf32 = tb["fused_w"].astype(np.float32).astype(np.float64)
+    A = morph.crushed_weights(wf32, 16, 8) if nd == 2 else morph.crushed_weights_3d(wf32, 8, 4, 4)
+    dense = morph.decompress_2_4(tb["a_hi"].astype(np.float64) + tb["a_lo"], tb["a_idx"])
+    assert morph.satisfies_2_4(dense)
+    order = tb["order"]
+    Ap = morph.apply_permutation(A, list(order))
+    if info.mma_terms == 4:
+        np.testing.assert_array_equal(dense, Ap)
+    else:
+        assert np.max(np.abs(dense - Ap)) <= 2.0 ** -15 * np.max(np.abs(A))
+    E = morph.conflict_graph(A)
+    for i in range(len(order) // 2):
+        a, b = int(order[2 * i]), int(order[2 * i + 1])
+        assert a == ZERO or b == ZERO or not E[a, b]
+    if info.pairing == 1:
+        pytest.importorskip("networkx")
+        _, zeros = morph.max_matching_pairs(A)
+        assert info.zero_columns == zeros
+
+
 def test_plans_of_one_stencil_share_tables(lib):
     """Planner tables depend on the stencil and the tile geometry, not on the grid's extents:
     plans of one stencil on grids of different sizes get the same tables (from the
