@@ -516,7 +516,7 @@ def main():
 
 
 # ---------------------------------------------------------------------------------------
-# Extra workloads (not the driver's JSON line): --suite, --batch, --serve print one JSON
+# Extra workloads (not the headline JSON line): --suite, --batch, --serve print one JSON
 # line per workload on stdout.
 # ---------------------------------------------------------------------------------------
 def _time_runs(fn, k=3, warm=1, flush=None):

@@ -40,7 +40,7 @@ typedef struct sparstencil_plan_s* sparstencil_plan_t; /* opaque, library-owned 
 typedef enum {
   SPST_OK = 0,
   SPST_ERR_INVALID = 1,      /* bad argument (null pointer, bad size, bad enum, ...) */
-  SPST_ERR_UNSUPPORTED = 2,  /* valid request outside what this build implements */
+  SPST_ERR_UNSUPPORTED = 2,  /* valid request outside what this library implements */
   SPST_ERR_NOMEM = 3,        /* device or host allocation failed, or workspace too small */
   SPST_ERR_CUDA = 4,         /* a CUDA runtime/driver call failed */
   SPST_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
