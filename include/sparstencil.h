@@ -107,7 +107,9 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
  * write-back; BF16 split keeps three weight pieces only where they fit beside them (with two
  * pieces its weight rounding, 2^-17, outweighs what the second accumulator saves).
  * Default: on for SPST_FP16_SPLIT plans where it fits (their operands hold 22 bits, so the
- * MMA roundings dominate), off otherwise.
+ * MMA roundings dominate) and for 3D SPST_BF16_SPLIT plans where it fits beside three weight
+ * pieces (a 3D step runs many more MMAs per output than a fused 2D or 1D step), off
+ * otherwise.
  * Must be called before the plan's first run (it rebuilds the host tables).
  * Errors: SPST_ERR_INVALID (null plan, single-word dtype, plan already ran),
  * SPST_ERR_UNSUPPORTED (the plan's fusion depth does not fit in TMEM this way; the plan is
