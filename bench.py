@@ -667,6 +667,35 @@ def ablation_mode():
         print(json.dumps(line), flush=True)
         del x, y, ref, work
         torch.cuda.empty_cache()
+    # the other dimensionalities at one size each: Box-2D9P 4096^2 (100 steps), Heat-3D 512^3
+    # (50 steps, FP16), Heat-1D 10,240,000 (1000 steps)
+    for name, dtype, T2 in (("box2d9p_4096", "bf16", 100), ("heat3d_512", "fp16", 50), ("heat1d", "bf16", 1000)):
+        cfg = inputs.CONFIGS[name]
+        dims = cfg["dims"]
+        nd = len(dims)
+        w2 = inputs.stencil_weights(cfg["shape"], nd, cfg["radius"], cfg["recipe"], seed=cfg["seed"])
+        x = torch.from_numpy(inputs.make_grid(cfg["grid"], cfg["seed"], dims)).cuda()
+        y, ref, work = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+        pts = T2 * int(np.prod(dims))
+        line = {"workload": f"{cfg['name'].split(',')[0]}, {cfg['bc']}, {T2} steps, {dtype}", "points": list(dims),
+                "steps": T2}
+        ms, _ = _time_runs(lambda: binding.direct_run(w2, x, ref, work, T2, bc=cfg["bc"]), 2, 1, flush)
+        line["fp32_direct_gstencil_s"] = pts / ms / 1e6
+        for tag, kw in (("dense_tc_t1", dict(fusion_depth=1, dense=True)), ("sparse_tc_t1", dict(fusion_depth=1)),
+                        ("sparse_tc_autotuned", dict(fusion_depth=0))):
+            try:
+                plan = binding.Plan(w2, dims, dtype=dtype, bc=cfg["bc"], shape=cfg["shape"], **kw)
+            except binding.SparStencilError as e:
+                line[tag] = f"unsupported: {e}"
+                continue
+            plan.run(x, y, T2)
+            ms, _ = _time_runs(lambda: plan.run(x, y, T2), 3, 1, flush)
+            line[f"{tag}_gstencil_s"] = pts / ms / 1e6
+            line[f"{tag}_fusion_depth"] = plan.info().fusion_depth
+            line[f"{tag}_rel_l2_vs_fp32_direct"] = _rel_l2_gpu(binding, y, ref)[0]
+        print(json.dumps(line), flush=True)
+        del x, y, ref, work
+        torch.cuda.empty_cache()
 
 
 def _c4c_jobs(n=64, seed=4):
