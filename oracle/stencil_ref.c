@@ -26,19 +26,23 @@
 #include <omp.h>
 #endif
 
+/* Largest weight cube (entries): 2D radius up to 31, 3D radius up to 7, 1D radius up to 2047. */
+#define ORACLE_MAX_CUBE 4096
+
 typedef struct {
   int npts;
-  int off[343][3]; /* offsets, padded to 3 axes (leading axes 0) */
-  double w[343];
+  int off[ORACLE_MAX_CUBE][3]; /* offsets, padded to 3 axes (leading axes 0) */
+  double w[ORACLE_MAX_CUBE];
 } stencil_pts;
 
 static int build_points(int ndim, int radius, const double* weights, stencil_pts* sp) {
+  if (radius > 2047) return -1;
   int side = 2 * radius + 1;
-  int total = 1;
+  int64_t total = 1;
   for (int i = 0; i < ndim; i++) total *= side;
-  if (total > 343) return -1;
+  if (total > ORACLE_MAX_CUBE) return -1;
   sp->npts = 0;
-  for (int idx = 0; idx < total; idx++) {
+  for (int idx = 0; idx < (int)total; idx++) {
     if (weights[idx] == 0.0) continue;
     int rem = idx;
     int o[3] = {0, 0, 0};
@@ -90,14 +94,18 @@ static void step(const int64_t d[3], const stencil_pts* sp, int bc, const double
 int oracle_stencil_run(int ndim, const int64_t* dims, int radius, const double* weights, int bc, int64_t T,
                        const double* in, double* out, double* scratch, int nthreads) {
   if (ndim < 1 || ndim > 3 || radius < 0 || T < 0 || (bc != 0 && bc != 1)) return -1;
-  stencil_pts sp;
-  if (build_points(ndim, radius, weights, &sp) != 0) return -1;
   int64_t d[3] = {1, 1, 1};
   int64_t n = 1;
   for (int i = 0; i < ndim; i++) {
     if (dims[i] <= 0) return -1;
     d[3 - ndim + i] = dims[i];
     n *= dims[i];
+  }
+  stencil_pts* sp = (stencil_pts*)malloc(sizeof(stencil_pts));
+  if (!sp) return -1;
+  if (build_points(ndim, radius, weights, sp) != 0) {
+    free(sp);
+    return -1;
   }
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -108,12 +116,13 @@ int oracle_stencil_run(int ndim, const int64_t* dims, int radius, const double* 
   double* a = out;
   double* b = scratch;
   for (int64_t s = 0; s < T; s++) {
-    step(d, &sp, bc, a, b);
+    step(d, sp, bc, a, b);
     double* t = a;
     a = b;
     b = t;
   }
   if (a != out) memcpy(out, a, (size_t)n * sizeof(double));
+  free(sp);
   return 0;
 }
 
@@ -125,8 +134,12 @@ int oracle_stencil_run(int ndim, const int64_t* dims, int radius, const double* 
 int oracle_stencil_point(int ndim, const int64_t* dims, int radius, const double* weights, int bc, int64_t T,
                          const double* in, const int64_t* point, double* value) {
   if (ndim < 1 || ndim > 3 || radius < 0 || T < 0 || (bc != 0 && bc != 1)) return -1;
-  stencil_pts sp;
-  if (build_points(ndim, radius, weights, &sp) != 0) return -1;
+  stencil_pts* sp = (stencil_pts*)malloc(sizeof(stencil_pts));
+  if (!sp) return -1;
+  if (build_points(ndim, radius, weights, sp) != 0) {
+    free(sp);
+    return -1;
+  }
   int64_t d[3] = {1, 1, 1}, p[3] = {0, 0, 0};
   for (int i = 0; i < ndim; i++) {
     d[3 - ndim + i] = dims[i];
@@ -143,6 +156,7 @@ int oracle_stencil_point(int ndim, const int64_t* dims, int radius, const double
     free(cur);
     free(nxt);
     free(outside);
+    free(sp);
     return -1;
   }
   int64_t hz = (3 - ndim > 0) ? 0 : h;
@@ -171,10 +185,10 @@ int oracle_stencil_point(int ndim, const int64_t* dims, int radius, const double
             continue;
           }
           double acc = 0.0;
-          for (int q = 0; q < sp.npts; q++) {
-            int64_t zz = z + sp.off[q][0], yy = y + sp.off[q][1], xx = x + sp.off[q][2];
+          for (int q = 0; q < sp->npts; q++) {
+            int64_t zz = z + sp->off[q][0], yy = y + sp->off[q][1], xx = x + sp->off[q][2];
             if (zz < 0 || zz >= wd[0] || yy < 0 || yy >= wd[1] || xx < 0 || xx >= wd[2]) continue;
-            acc += sp.w[q] * cur[(zz * wd[1] + yy) * wd[2] + xx];
+            acc += sp->w[q] * cur[(zz * wd[1] + yy) * wd[2] + xx];
           }
           nxt[wi] = acc;
         }
@@ -186,5 +200,6 @@ int oracle_stencil_point(int ndim, const int64_t* dims, int radius, const double
   free(cur);
   free(nxt);
   free(outside);
+  free(sp);
   return 0;
 }

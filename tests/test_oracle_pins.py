@@ -133,7 +133,10 @@ def test_dense_matrix_pinned_by_fft():
 
 @pytest.mark.parametrize("dims,r,bc,T", [((5, 6), 1, "dirichlet", 4), ((5, 6), 1, "periodic", 5),
                                          ((7, 5), 2, "dirichlet", 3), ((4, 5, 3), 1, "periodic", 3),
-                                         ((3, 4, 5), 1, "dirichlet", 4), ((11,), 2, "periodic", 6)])
+                                         ((3, 4, 5), 1, "dirichlet", 4), ((11,), 2, "periodic", 6),
+                                         # the widest cubes the planner accepts: 2D radius 9, 1D radius 60
+                                         ((23, 25), 9, "periodic", 2), ((21, 22), 9, "dirichlet", 2),
+                                         ((150,), 60, "periodic", 2), ((130,), 60, "dirichlet", 2)])
 def test_brute_force_matrix_power(oracle_mod, dims, r, bc, T):
     """Tiny grids: the oracle equals S^T u with S the dense stencil matrix."""
     rng = _rng(sum(dims) + r + T)
@@ -177,6 +180,47 @@ def test_zero_steps_is_identity(oracle_mod):
     u = _rng(5).random((6, 7))
     w = _rng(6).random((3, 3))
     np.testing.assert_array_equal(oracle_mod.run(u, w, "dirichlet", 0), u)
+
+
+def _shifted(u, axis, step, bc):
+    """u translated so that out[i] = u[i + step * e_axis]; zero where that leaves the grid
+    under a Dirichlet boundary."""
+    if bc == "periodic":
+        return np.roll(u, -step, axis=axis)
+    out = np.zeros_like(u)
+    n = u.shape[axis]
+    src = [slice(None)] * u.ndim
+    dst = [slice(None)] * u.ndim
+    if step >= 0:
+        src[axis], dst[axis] = slice(step, n), slice(0, max(n - step, 0))
+    else:
+        src[axis], dst[axis] = slice(0, max(n + step, 0)), slice(-step, n)
+    out[tuple(dst)] = u[tuple(src)]
+    return out
+
+
+@pytest.mark.parametrize("ndim,dims", [(1, (23,)), (2, (9, 11)), (3, (5, 6, 7))])
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+def test_degenerate_stencils_are_exact(oracle_mod, ndim, dims, bc):
+    """Degenerate stencils of Sec. 2.2's update: all weights zero gives zeros; the centre
+    weight alone gives the input back; a single unit weight at offset +-1 along one axis
+    translates the grid by T cells per T steps (a plain array shift, zeros entering under a
+    Dirichlet boundary).  Every value is exact in FP64.  A wrong axis, offset sign or
+    boundary rule moves cells and fails this."""
+    u = _rng(9).random(dims)
+    T = 4
+    zero = np.zeros((3,) * ndim)
+    assert np.all(oracle_mod.run(u, zero, bc, T) == 0.0)
+    ident = zero.copy()
+    ident[(1,) * ndim] = 1.0
+    np.testing.assert_array_equal(oracle_mod.run(u, ident, bc, T), u)
+    for axis in range(ndim):
+        for sign in (1, -1):
+            w = zero.copy()
+            idx = [1] * ndim
+            idx[axis] = 1 + sign
+            w[tuple(idx)] = 1.0
+            np.testing.assert_array_equal(oracle_mod.run(u, w, bc, T), _shifted(u, axis, sign * T, bc))
 
 
 def test_rel_errors(oracle_mod):
