@@ -478,3 +478,62 @@ def test_custom_mask_matches_oracle(torch_cuda, oracle_mod, name, dims, steps, b
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
     assert l2 <= TOL[dtype], (l2, linf, plan.info().pairing)
+
+
+@pytest.mark.parametrize("ndim,dims,bc,t,steps", [
+    (1, (40000,), "periodic", 3, 6),
+    (1, (40000,), "dirichlet", 1, 3),
+    (2, (200, 296), "periodic", 3, 6),
+    (2, (200, 296), "dirichlet", 3, 6),
+    (3, (40, 36, 72), "periodic", 1, 2),
+    (3, (40, 36, 72), "dirichlet", 1, 2),
+])
+@pytest.mark.parametrize("dtype", ["bf16", "bf16_split", "fp16", "fp16_split"])
+def test_degenerate_stencils(torch_cuda, oracle_mod, ndim, dims, bc, t, steps, dtype):
+    """Degenerate stencils (ragged grids, fused sweeps where the plan allows them): all
+    weights zero gives exact zeros; the centre weight alone returns the input; a unit weight
+    at offset +1 along the last axis or -1 along the first translates the grid (the oracle's
+    exact shift), each within the dtype's tolerance."""
+    u = inputs.uniform01(7, dims)
+    zero = np.zeros((3,) * ndim, np.float32)
+    got, _ = _run_sparse(torch_cuda, u, zero, steps, dtype, bc, t, "box")
+    assert np.all(got == 0.0)
+    cases = []
+    ident = zero.copy()
+    ident[(1,) * ndim] = 1.0
+    cases.append(ident)
+    for axis, sign in ((ndim - 1, 1), (0, -1)):
+        w = zero.copy()
+        idx = [1] * ndim
+        idx[axis] = 1 + sign
+        w[tuple(idx)] = 1.0
+        cases.append(w)
+    for w in cases:
+        ref = oracle_mod.run(u, w, bc, steps)
+        got, plan = _run_sparse(torch_cuda, u, w, steps, dtype, bc, t, "box")
+        assert plan.info().fusion_depth == t
+        l2, linf = oracle_mod.rel_errors(got, ref)
+        assert np.all(np.isfinite(got))
+        assert l2 <= TOL[dtype], (np.argwhere(w).tolist(), l2, linf)
+
+
+@pytest.mark.parametrize("ndim,shape,r,dims,steps,bc,dtype,t", [
+    (2, "box", 6, (300, 260), 3, "periodic", "bf16_split", 1),
+    (2, "box", 6, (260, 300), 3, "dirichlet", "fp16", 1),
+    (2, "star", 9, (300, 260), 3, "periodic", "bf16_split", 1),
+    (2, "star", 4, (300, 260), 4, "periodic", "bf16", 2),
+    (1, "box", 60, (40000,), 4, "periodic", "bf16_split", 1),
+    (1, "star", 30, (40000,), 4, "periodic", "fp16_split", 2),
+])
+def test_widest_stencils_match_oracle(torch_cuda, oracle_mod, ndim, shape, r, dims, steps, bc, dtype, t):
+    """The widest stencils whose tables fit TMEM (2D: a 13 x 13 box or a radius-9 star,
+    K_pad = 576; a radius-4 star fused to radius 8; 1D: fused radius 60) match the oracle
+    at the dtype's tolerance."""
+    w = inputs.stencil_weights(shape, ndim, r, "gaussian", seed=17)
+    u = inputs.uniform01(12, dims)
+    ref = oracle_mod.run(u, w, bc, steps)
+    got, plan = _run_sparse(torch_cuda, u, w, steps, dtype, bc, t, shape)
+    assert plan.info().fusion_depth == t
+    l2, linf = oracle_mod.rel_errors(got, ref)
+    assert np.all(np.isfinite(got))
+    assert l2 <= TOL[dtype], (l2, linf, plan.info().kpad)
