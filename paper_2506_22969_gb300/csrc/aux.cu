@@ -59,8 +59,14 @@ __device__ __forceinline__ void copy_padded_row(const float* __restrict__ src, f
   }
 }
 
+// Lets the next sweep (launched with programmatic stream serialization) start its set-up
+// while this kernel runs; the sweep reads the grids only after its griddepcontrol.wait,
+// which waits for this kernel to complete and its writes to be visible.
+__device__ __forceinline__ void allow_next_sweep() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 __global__ void pad_copy2d_kernel(const float* __restrict__ in, float* __restrict__ out, int H, int W, int G,
                                   int64_t Wp, int periodic, unsigned* maxabs) {
+  allow_next_sweep();
   // a CTA per padded row (grid-stride over rows), its threads along x
   const int64_t Hp = (int64_t)H + 2 * G;
   float m = 0.f;
@@ -80,6 +86,7 @@ __global__ void pad_copy2d_kernel(const float* __restrict__ in, float* __restric
 
 __global__ void pad_copy1d_kernel(const float* __restrict__ in, float* __restrict__ out, int64_t W, int G,
                                   int64_t Wp, int periodic, unsigned* maxabs) {
+  allow_next_sweep();
   // block b copies segment [b * 1024, (b + 1) * 1024) of the padded line (grid-stride)
   float m = 0.f;
   constexpr int64_t kSeg = 1024;
@@ -115,6 +122,7 @@ __global__ void pad_copy1d_kernel(const float* __restrict__ in, float* __restric
 // Periodic 1D ghosts: cell i < G holds x = i - G, the image of x + W; cell W + G + i holds
 // x = W + i, the image of i.
 __global__ void ghost_refresh1d_kernel(float* line, int64_t W, int G) {
+  allow_next_sweep();
   for (int i = threadIdx.x; i < G; i += blockDim.x) {
     line[i] = line[i + W];
     line[W + G + i] = line[G + i];
@@ -363,6 +371,7 @@ __global__ void norms_kernel(const float* __restrict__ x, const float* __restric
 // the rectangle.
 // ---------------------------------------------------------------------------------------
 __global__ void band2d_kernel(const BandParams p) {
+  allow_next_sweep();
   extern __shared__ float bsm[];
   const int H = p.H, W = p.W, bw = p.bw, seg = p.seg, r = p.radius;
   const int top_h = bw < H ? bw : H;
@@ -425,6 +434,7 @@ __global__ void band2d_kernel(const BandParams p) {
 // ---------------------------------------------------------------------------------------
 __global__ void pad_copy3d_kernel(const float* __restrict__ in, float* __restrict__ out, int D, int H, int W, int G,
                                   int64_t Wp, int periodic, unsigned* maxabs) {
+  allow_next_sweep();
   // a CTA per padded row (grid-stride over rows), its threads along x: the row's source row
   // is found once, and loads and stores are contiguous
   const int64_t Hp = (int64_t)H + 2 * G, Dp = (int64_t)D + 2 * G;
@@ -450,6 +460,7 @@ __global__ void pad_copy3d_kernel(const float* __restrict__ in, float* __restric
 // sweep that wrote the interior only).  One thread per padded cell of each padded row; rows
 // wholly in the interior only touch their 2G ghost columns.
 __global__ void ghost_refresh3d_kernel(float* __restrict__ g3, int D, int H, int W, int G, int64_t Wp) {
+  allow_next_sweep();
   const int64_t Hp = (int64_t)H + 2 * G, Dp = (int64_t)D + 2 * G;
   const int64_t rows = Dp * Hp;
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {

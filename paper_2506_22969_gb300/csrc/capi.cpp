@@ -265,7 +265,11 @@ const SweepTables* tables_for(sparstencil_plan_t p, int depth, std::string* err)
   return &(p->rem[depth] = std::move(T));
 }
 
-sparstencil_status ensure_device_tables(sparstencil_plan_t p, int depth, const SweepTables& T, DeviceTables** out) {
+// Uploads a depth's tables on first use.  The copies are ordered on `stream`, ahead of the
+// kernels that read them (the host vectors are pageable: each copy is staged before the
+// call returns).
+sparstencil_status ensure_device_tables(sparstencil_plan_t p, int depth, const SweepTables& T, DeviceTables** out,
+                                        cudaStream_t stream) {
   auto& dt = p->dev_tables[depth];
   if (!dt.lut) {
     const std::vector<uint32_t> dense_words = p->dense ? spst::dense_a_words(T, word_of(p->dtype)) : std::vector<uint32_t>();
@@ -273,9 +277,9 @@ sparstencil_status ensure_device_tables(sparstencil_plan_t p, int depth, const S
     SPST_CUDA(cudaMalloc(&dt.lut, T.lut.size() * 4), "cudaMalloc(lut)");
     SPST_CUDA(cudaMalloc(&dt.a_words, aw.size() * 4), "cudaMalloc(a_words)");
     SPST_CUDA(cudaMalloc(&dt.meta, T.meta_words.size() * 4), "cudaMalloc(meta)");
-    SPST_CUDA(cudaMemcpy(dt.lut, T.lut.data(), T.lut.size() * 4, cudaMemcpyHostToDevice), "upload lut");
-    SPST_CUDA(cudaMemcpy(dt.a_words, aw.data(), aw.size() * 4, cudaMemcpyHostToDevice), "upload A''");
-    SPST_CUDA(cudaMemcpy(dt.meta, T.meta_words.data(), T.meta_words.size() * 4, cudaMemcpyHostToDevice),
+    SPST_CUDA(cudaMemcpyAsync(dt.lut, T.lut.data(), T.lut.size() * 4, cudaMemcpyHostToDevice, stream), "upload lut");
+    SPST_CUDA(cudaMemcpyAsync(dt.a_words, aw.data(), aw.size() * 4, cudaMemcpyHostToDevice, stream), "upload A''");
+    SPST_CUDA(cudaMemcpyAsync(dt.meta, T.meta_words.data(), T.meta_words.size() * 4, cudaMemcpyHostToDevice, stream),
               "upload metadata");
   }
   *out = &dt;
@@ -503,6 +507,15 @@ cudaError_t after_sweep(sparstencil_plan_t p, int depth, const float* src, const
 sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStream_t stream) {
   int* status = spst::device_status_word();
   if (!status) return fail(SPST_ERR_CUDA, "device status word unavailable");
+  // every depth's tables are uploaded ahead of the copy-in kernel, so that no copy sits
+  // between two sweeps (a sweep's set-up may overlap the kernel before it)
+  for (int depth = 1; depth <= p->t_max; depth++) {
+    std::string err;
+    const SweepTables* T = tables_for(p, depth, &err);
+    DeviceTables* dt = nullptr;
+    sparstencil_status su = T ? ensure_device_tables(p, depth, *T, &dt, stream) : SPST_OK;
+    if (su != SPST_OK) return su;
+  }
   SPST_CUDA(copy_in(p, in, p->pad(0), 3 * p->t_max, stream, p->maxabs), "pad copy");
   cudaEvent_t e0, e1;
   SPST_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
@@ -518,7 +531,7 @@ sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStr
     const SweepTables* T = tables_for(p, depth, &err);
     if (!T) continue;
     DeviceTables* dt = nullptr;
-    if ((s = ensure_device_tables(p, depth, *T, &dt)) != SPST_OK) break;
+    if ((s = ensure_device_tables(p, depth, *T, &dt, stream)) != SPST_OK) break;
     int cur = 0;
     float ms = 0.f;
     for (int k = 0; k < 3 && s == SPST_OK; k++) {
@@ -582,7 +595,7 @@ sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out,
     std::string err;
     tabs[i] = tables_for(p, sweeps[i], &err);
     if (!tabs[i]) return fail(SPST_ERR_UNSUPPORTED, err);
-    s = ensure_device_tables(p, sweeps[i], *tabs[i], &dtabs[i]);
+    s = ensure_device_tables(p, sweeps[i], *tabs[i], &dtabs[i], stream);
     if (s != SPST_OK) return s;
   }
   // a run that the caller captures into a CUDA graph launches in plain stream order (the
@@ -1010,7 +1023,7 @@ sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const 
       const SweepTables* T = tables_for(p, d, &err);
       if (!T) return fail(SPST_ERR_UNSUPPORTED, err);
       DeviceTables* dt = nullptr;
-      if ((s = ensure_device_tables(p, d, *T, &dt)) != SPST_OK) return s;
+      if ((s = ensure_device_tables(p, d, *T, &dt, stream)) != SPST_OK) return s;
     }
   }
   SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
