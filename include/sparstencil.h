@@ -137,7 +137,7 @@ sparstencil_status sparstencil_plan_set_dense_ablation(sparstencil_plan_t plan, 
  * returns.  Calls on one plan must not overlap on the GPU (they share the workspace).
  * A run may be captured into a CUDA graph (stream capture on `stream`) once the plan has run
  * once with the same timesteps (workspace and tables on the device, fusion depth chosen);
- * inside a capture the sweeps launch in plain stream order. */
+ * the capture records the sweeps' programmatic dependent launches as programmatic edges. */
 sparstencil_status sparstencil_run(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
                                    cudaStream_t stream);
 
