@@ -63,9 +63,10 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _profile_traffic():
+def _profile_traffic(depth: int):
     """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary, if the
-    summary was taken on the current kernel source (sweep2d.cu + kernels.h; else None)."""
+    summary was taken on the current kernel source (sweep2d.cu + kernels.h) at the timed
+    fusion depth (else None)."""
     csrc = os.path.join(ROOT, "paper_2506_22969_gb300", "csrc")
     prof = os.path.join(ROOT, "profiles", "sweep2d_box9_4096.md")
     try:
@@ -78,7 +79,8 @@ def _profile_traffic():
             text = f.read()
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
         m_tr = re.search(r"dram_bytes_per_launch_scaled:\s*([0-9.eE+]+)", text)
-        if m_sha and m_tr and m_sha.group(1) == sha:
+        m_t = re.search(r"fusion_depth:\s*([0-9]+)", text)
+        if m_sha and m_tr and m_t and m_sha.group(1) == sha and int(m_t.group(1)) == depth:
             return float(m_tr.group(1))
     except OSError:
         pass
@@ -379,7 +381,9 @@ def main():
 
     # autotune the fusion depth per precision (the paper's layout search rebuilt as a
     # measured search over the fused depth t)
-    candidates = [args.fusion] if args.fusion > 0 else [1, 2, 3]
+    # (the library's own search range in 2D: depths 1-6; depths whose tables do not fit TMEM
+    # or shared memory are rejected by the planner and skipped)
+    candidates = [args.fusion] if args.fusion > 0 else [1, 2, 3, 4, 5, 6]
     tune = {}
 
     # the Sec. 3.3 cost model beside the measured search: sparse tensor rate = 2 x the measured
@@ -392,7 +396,10 @@ def main():
         tune[dtype] = {}
         model[dtype] = {}
         for t in candidates:
-            pl = binding.Plan(w, (H, W), dtype=dtype, bc=cfg["bc"], fusion_depth=t, shape=cfg["shape"])
+            try:
+                pl = binding.Plan(w, (H, W), dtype=dtype, bc=cfg["bc"], fusion_depth=t, shape=cfg["shape"])
+            except binding.SparStencilError:
+                continue
             ms = min(timed_runs(lambda: pl.run(x, y, T), 2, 1))
             tune[dtype][str(t)] = ms
             model[dtype][str(t)] = pl.cost_model(t, *model_rates) * T * 1e3
@@ -443,7 +450,7 @@ def main():
     alg_bytes = 8.0 * H * W  # read 4 B + write 4 B per output per sweep
     achieved = alg_bytes / (sweep_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _profile_traffic()
+    traffic = _profile_traffic(t_best)
 
     rel_split = sampled_rel_l2(y)
 

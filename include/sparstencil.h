@@ -85,8 +85,9 @@ typedef struct {
  *   weights: host FP32 cube (see conventions), copied; for SPST_STAR/SPST_BOX only the
  *            shape's points may be nonzero (checked), SPST_CUSTOM accepts any support.
  *   fusion_depth: t >= 1 fuses t steps per sweep; 0 lets the library choose: the plan
- *            takes the deepest of 3, 2, 1 (1D periodic: of min(8, 60 / radius) down to 1)
- *            whose tables fit, and the first sparstencil_run
+ *            takes the deepest depth whose tables fit TMEM and shared memory, searched
+ *            from 6 down to 1 in 2D, from min(8, 60 / radius) in 1D and from 3 in 3D
+ *            (Dirichlet fusion: 2D, radius <= 4), and the first sparstencil_run
  *            times two sweeps of every depth up to it on its own input (after one warm-up
  *            sweep each; that call synchronises its stream once) and keeps the depth with the
  *            least time per step.  sparstencil_query reports the planned maximum until then.

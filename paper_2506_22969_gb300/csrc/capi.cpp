@@ -181,8 +181,40 @@ std::string tables_cached(const std::vector<double>& wf, int R, const PlanGeomet
   return "";
 }
 
+// Inputs one patch's outputs read through the composed stencil wf of radius R (the nonzero
+// columns of A', a lower bound on K_pad): |patch + support(wf)|, counted on a bitmap.
+int64_t patch_inputs(const std::vector<double>& wf, int ndim, int R) {
+  const int kt = 2 * R + 1;
+  const int r1 = ndim == 1 ? Tile1D::R1 : ndim == 2 ? Tile2D::R1 : Tile3D::R1;
+  const int r2 = ndim == 1 ? 1 : ndim == 2 ? Tile2D::R2 : Tile3D::R2;
+  const int r3 = ndim == 3 ? Tile3D::R3 : 1;
+  const int kz = ndim == 3 ? kt : 1, ky = ndim >= 2 ? kt : 1;
+  const int bx = r1 + kt - 1, by = r2 + ky - 1, bz = r3 + kz - 1;
+  std::vector<char> hit((size_t)bx * by * bz, 0);
+  for (int z = 0; z < kz; z++)
+    for (int y = 0; y < ky; y++)
+      for (int x = 0; x < kt; x++) {
+        if (wf[((size_t)z * ky + y) * kt + x] == 0.0) continue;
+        for (int oz = 0; oz < r3; oz++)
+          for (int oy = 0; oy < r2; oy++)
+            for (int ox = 0; ox < r1; ox++) hit[((size_t)(z + oz) * by + (y + oy)) * bx + (x + ox)] = 1;
+      }
+  int64_t n = 0;
+  for (char h : hit) n += h;
+  return n;
+}
+
 std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
   std::vector<double> wf = spst::compose_weights(p->w64, p->ndim, p->radius, depth);
+  {
+    // cheap rejection before the matching: even with the fewest pieces (two) and no zero
+    // columns, K_pad >= the patch's input count, and the A'' pieces, metadata and one
+    // accumulator must fit the 512 TMEM columns
+    const int64_t kmin = (patch_inputs(wf, p->ndim, depth * p->radius) + 31) / 32 * 32;
+    const int64_t need = (p->dense ? 2 * (kmin / 2) : 2 * (kmin / 4) + 8 * ((kmin / 32 + 1) / 2)) +
+                         (p->lo_acc ? 256 : 128);
+    if (need > 512) return std::string("stencil too wide for TMEM (kpad >= ") + std::to_string(kmin) + ")";
+  }
   // Weight pieces: single-word operands use two 16-bit pieces.  BF16 split operands use three
   // (exact for FP32 weights); FP16 split operands two, which hold 22 significant bits of each
   // scaled weight: a third FP16 piece sits below the rounding of the FP32 accumulator it is
@@ -801,7 +833,7 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   // fusion_depth 0: the deepest of 3, 2, 1 whose tables fit is planned; the first run times
   // every depth up to it and keeps the fastest per time step
   // 1D: K grows by only 2r columns per fused step (k' = kt + 127), so deeper fusion is searched
-  const int t_deep = ndim == 1 ? std::max(1, std::min(8, 60 / radius)) : 3;
+  const int t_deep = ndim == 1 ? std::max(1, std::min(8, 60 / radius)) : ndim == 2 ? 6 : 3;
   const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && (radius > 4 || ndim != 2)) ? 1 : t_deep) : p->t;
   const int side = 2 * radius + 1;
   p->w64.resize((size_t)side * (ndim >= 2 ? side : 1) * (ndim == 3 ? side : 1));

@@ -256,11 +256,19 @@ def test_cost_model_orders_layouts():
 
 
 def test_autotune_plan_takes_the_deepest_depth_that_fits(lib):
-    """fusion_depth 0 plans the deepest of 3, 2, 1 whose tables fit (the first run then
-    times each depth up to it)."""
+    """fusion_depth 0 plans the deepest depth whose tables fit (2D: of 6 down to 1; the first
+    run then times each depth up to it)."""
     w = inputs.stencil_weights("box", 2, 1, "random", seed=2)
     p = binding.Plan(w, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=0)
-    assert p.info().fusion_depth == 3 and p.info().ghost == 3
+    # 3x3 box: t = 6 (K_pad 576) fits; t = 7 (K_pad 672) would not, and is not searched
+    assert p.info().fusion_depth == 6 and p.info().ghost == 6 and p.info().kpad == 576
+    with pytest.raises(binding.SparStencilError) as e:
+        binding.Plan(w, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=7)
+    assert e.value.code == 2
+    # 5x5 box: t = 3 (fused radius 6, K_pad 576) is the deepest that fits
+    w2 = inputs.stencil_weights("box", 2, 2, "random", seed=2)
+    p2 = binding.Plan(w2, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=0)
+    assert p2.info().fusion_depth == 3 and p2.info().kpad == 576
     # 7x7 box, split: t = 3 (K_pad 960) does not fit TMEM; t = 2 (K_pad 576) fits with two
     # BF16 weight pieces beside one accumulator
     w3 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=2)
