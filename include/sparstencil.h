@@ -86,9 +86,10 @@ typedef struct {
  *            shape's points may be nonzero (checked), SPST_CUSTOM accepts any support.
  *   fusion_depth: t >= 1 fuses t steps per sweep; 0 lets the library choose: the plan
  *            takes the deepest depth whose tables fit TMEM and shared memory, searched
- *            from 6 down to 1 in 2D, from min(8, 60 / radius) in 1D and from 3 in 3D
+ *            from 6 down to 1 in 2D, from 60 / radius in 1D and from 3 in 3D
  *            (Dirichlet fusion: 2D, radius <= 4), and the first sparstencil_run
- *            times two sweeps of every depth up to it on its own input (after one warm-up
+ *            times two sweeps of every depth up to it (1D: of the powers of two below it and
+ *            of the maximum) on its own input (after one warm-up
  *            sweep each; that call synchronises its stream once) and keeps the depth with the
  *            least time per step.  sparstencil_query reports the planned maximum until then.
  *   out_plan: receives the plan (owned by the library until sparstencil_plan_destroy).

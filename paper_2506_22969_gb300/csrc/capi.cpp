@@ -536,12 +536,22 @@ cudaError_t after_sweep(sparstencil_plan_t p, int depth, const float* src, const
   return launch_band(p, depth, src, prm.out, prm.out_pitch, prm.out_off, stream);
 }
 
+// Depths the first run of an autotuned plan times: every depth up to the plan's maximum, or
+// in 1D (where the maximum reaches 60 / radius) the powers of two below it and the maximum.
+std::vector<int> autotune_depths(const sparstencil_plan_s* p) {
+  std::vector<int> d;
+  for (int t = 1; t <= p->t_max; t = p->geo.ndim == 1 ? 2 * t : t + 1) d.push_back(t);
+  if (d.back() != p->t_max) d.push_back(p->t_max);
+  return d;
+}
+
 sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStream_t stream) {
   int* status = spst::device_status_word();
   if (!status) return fail(SPST_ERR_CUDA, "device status word unavailable");
   // every depth's tables are uploaded ahead of the copy-in kernel, so that no copy sits
   // between two sweeps (a sweep's set-up may overlap the kernel before it)
-  for (int depth = 1; depth <= p->t_max; depth++) {
+  const std::vector<int> depths = autotune_depths(p);
+  for (int depth : depths) {
     std::string err;
     const SweepTables* T = tables_for(p, depth, &err);
     DeviceTables* dt = nullptr;
@@ -558,7 +568,8 @@ sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStr
   int best = p->t;
   double best_ms = 1e300;
   sparstencil_status s = SPST_OK;
-  for (int depth = 1; depth <= p->t_max && s == SPST_OK; depth++) {
+  for (size_t di = 0; di < depths.size() && s == SPST_OK; di++) {
+    const int depth = depths[di];
     std::string err;
     const SweepTables* T = tables_for(p, depth, &err);
     if (!T) continue;
@@ -833,7 +844,7 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   // fusion_depth 0: the deepest of 3, 2, 1 whose tables fit is planned; the first run times
   // every depth up to it and keeps the fastest per time step
   // 1D: K grows by only 2r columns per fused step (k' = kt + 127), so deeper fusion is searched
-  const int t_deep = ndim == 1 ? std::max(1, std::min(8, 60 / radius)) : ndim == 2 ? 6 : 3;
+  const int t_deep = ndim == 1 ? std::max(1, 60 / radius) : ndim == 2 ? 6 : 3;
   const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && (radius > 4 || ndim != 2)) ? 1 : t_deep) : p->t;
   const int side = 2 * radius + 1;
   p->w64.resize((size_t)side * (ndim >= 2 ? side : 1) * (ndim == 3 ? side : 1));
