@@ -412,6 +412,9 @@ CASES_1D = [
     ("box", 2, "random", 70000, 9, "dirichlet", "fp16_split", 1),
     ("star", 1, "random", 300, 5, "periodic", "bf16", 1),
     ("box", 3, "gaussian", 40000, 16, "periodic", "bf16_split", 0),
+    # deep 1D fusion (fused radius 60) with a remainder sweep
+    ("star", 1, "heat", 3 * 16384 + 100, 130, "periodic", "fp16", 60),
+    ("box", 2, "random", 50000, 70, "periodic", "bf16_split", 30),
 ]
 
 
