@@ -271,6 +271,10 @@ def test_autotune_plan_takes_the_deepest_depth_that_fits(lib):
     assert p1.info().fusion_depth == 60 and p1.info().ghost == 60 and p1.info().kpad == 256
     w12 = inputs.stencil_weights("box", 1, 2, "random", seed=2)
     assert binding.Plan(w12, (100000,), dtype="fp16", bc="periodic", fusion_depth=0).info().fusion_depth == 30
+    # a depth whose patch input count alone cannot fit TMEM is rejected before any matching
+    with pytest.raises(binding.SparStencilError) as e:
+        binding.Plan(w, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=20)
+    assert e.value.code == 2 and "kpad >= 2688" in str(e.value)
     # 5x5 box: t = 3 (fused radius 6, K_pad 576) is the deepest that fits
     w2 = inputs.stencil_weights("box", 2, 2, "random", seed=2)
     p2 = binding.Plan(w2, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=0)
