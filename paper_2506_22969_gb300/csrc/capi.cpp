@@ -841,9 +841,10 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   if (bc == SPST_DIRICHLET_ZERO && p->t > 1 && (radius > 4 || ndim != 2))
     return fail(SPST_ERR_UNSUPPORTED, "temporal fusion with a Dirichlet boundary needs a 2D grid and radius <= 4");
   p->t_max = p->t;
-  // fusion_depth 0: the deepest of 3, 2, 1 whose tables fit is planned; the first run times
-  // every depth up to it and keeps the fastest per time step
-  // 1D: K grows by only 2r columns per fused step (k' = kt + 127), so deeper fusion is searched
+  // fusion_depth 0: the deepest depth whose tables fit is planned (searched down from 6 in 2D,
+  // 3 in 3D); the first run times the depths up to it and keeps the fastest per time step.
+  // 1D: K grows by only 2r columns per fused step (k' = kt + 127), so the search starts at the
+  // largest fused radius the tiles allow (60)
   const int t_deep = ndim == 1 ? std::max(1, 60 / radius) : ndim == 2 ? 6 : 3;
   const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && (radius > 4 || ndim != 2)) ? 1 : t_deep) : p->t;
   const int side = 2 * radius + 1;
