@@ -121,6 +121,16 @@ def point(u0, weights, bc, T: int, index) -> float:
     return float(val.value)
 
 
+def points(u0, weights, bc, T: int, indices, threads: int = 0) -> np.ndarray:
+    """:func:`point` at many grid points, evaluated concurrently on host threads (the C
+    routine keeps no shared state, and ctypes releases the GIL while it runs)."""
+    from concurrent.futures import ThreadPoolExecutor
+    u = np.ascontiguousarray(np.asarray(u0, dtype=np.float64))  # converted once, shared
+    n = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=n) as ex:
+        return np.array(list(ex.map(lambda p: point(u, weights, bc, T, p), list(indices))), dtype=np.float64)
+
+
 def rel_errors(x, ref):
     """rel-L2 = ||x-ref||_2/||ref||_2 and rel-Linf = max|x-ref|/max|ref|, in FP64."""
     x = np.asarray(x, dtype=np.float64)

@@ -128,9 +128,10 @@ int oracle_stencil_run(int ndim, const int64_t* dims, int radius, const double* 
 
 /* Value of one grid point after T steps, from the dependence cone only: a window of
  * half-width T*r around the point (periodic: wrapped coordinates; Dirichlet: points
- * outside the grid are held at zero).  Window cells whose neighbours leave the window
- * read 0; that error travels inwards r cells per step and never reaches the centre.
- * Returns 0 on success. */
+ * outside the grid are held at zero).  Step s (s = 0 .. T-1) updates only the cells within
+ * (T-1-s)*r of the point along every axis: those are the cells a later step reads, and each
+ * reads neighbours within (T-s)*r, all updated by the step before (or initial values), so
+ * every value computed is the full-grid value of that cell.  Returns 0 on success. */
 int oracle_stencil_point(int ndim, const int64_t* dims, int radius, const double* weights, int bc, int64_t T,
                          const double* in, const int64_t* point, double* value) {
   if (ndim < 1 || ndim > 3 || radius < 0 || T < 0 || (bc != 0 && bc != 1)) return -1;
@@ -176,9 +177,12 @@ int oracle_stencil_point(int ndim, const int64_t* dims, int radius, const double
         }
       }
   for (int64_t s = 0; s < T; s++) {
-    for (int64_t z = 0; z < wd[0]; z++)
-      for (int64_t y = 0; y < wd[1]; y++)
-        for (int64_t x = 0; x < wd[2]; x++) {
+    const int64_t keep = (T - 1 - s) * radius; /* half-width of the cells still needed */
+    const int64_t z0 = hz - (hz ? keep : 0), z1 = hz + (hz ? keep : 0);
+    const int64_t y0 = hy - (hy ? keep : 0), y1 = hy + (hy ? keep : 0);
+    for (int64_t z = z0; z <= z1; z++)
+      for (int64_t y = y0; y <= y1; y++)
+        for (int64_t x = h - keep; x <= h + keep; x++) {
           int64_t wi = (z * wd[1] + y) * wd[2] + x;
           if (outside[wi]) {
             nxt[wi] = 0.0;

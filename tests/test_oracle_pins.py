@@ -161,12 +161,14 @@ def test_constant_field_invariant(oracle_mod):
     assert np.all(outd[0, :] < 0.75 * s ** T)
 
 
-@pytest.mark.parametrize("ndim,bc", [(2, "periodic"), (2, "dirichlet"), (3, "dirichlet"), (3, "periodic")])
+@pytest.mark.parametrize("ndim,bc", [(1, "periodic"), (1, "dirichlet"), (2, "periodic"), (2, "dirichlet"),
+                                     (3, "dirichlet"), (3, "periodic")])
 def test_point_oracle_matches_full(oracle_mod, ndim, bc):
-    """The dependence-cone point oracle equals the full-grid oracle (both boundaries)."""
+    """The dependence-cone point oracle equals the full-grid oracle (both boundaries; the
+    cone's half-width T*r exceeds the grid, so periodic windows wrap more than once)."""
     rng = _rng(11 + ndim)
-    dims = (19, 23) if ndim == 2 else (9, 10, 11)
-    r, T = (2, 4) if ndim == 2 else (1, 3)
+    dims = {1: (37,), 2: (19, 23), 3: (9, 10, 11)}[ndim]
+    r, T = {1: (3, 9), 2: (2, 7), 3: (1, 6)}[ndim]
     w = rng.random((2 * r + 1,) * ndim)
     u = rng.random(dims)
     full = oracle_mod.run(u, w, bc, T)
