@@ -58,7 +58,7 @@ typedef enum { SPST_DIRICHLET_ZERO = 0, SPST_PERIODIC = 1 } sparstencil_boundary
 
 /* Description of a plan (sparstencil_query). */
 typedef struct {
-  int ndim;            /* 2 or 3 */
+  int ndim;            /* 1, 2 or 3 */
   int radius;          /* stencil radius r */
   int fusion_depth;    /* t: time steps fused per sweep (composed kernel of radius t*r) */
   int r1, r2, r3;      /* crush factors (outputs per patch along x, y, z); r1*r2*r3 = 128 */
@@ -94,7 +94,7 @@ typedef struct {
  *            least time per step.  sparstencil_query reports the planned maximum until then.
  *   out_plan: receives the plan (owned by the library until sparstencil_plan_destroy).
  * Host only (no device work).  Errors: SPST_ERR_INVALID, SPST_ERR_UNSUPPORTED
- * (ndim not 2/3, radius too large for TMEM, ...), SPST_ERR_NOMEM.
+ * (ndim not 1, 2 or 3, radius too large for TMEM, ...), SPST_ERR_NOMEM.
  * Follows the problem statement of Sec. 2.2 and the planning steps of Sec. 3.1-3.3. */
 sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const float* weights, int ndim,
                                     const int64_t* dims, sparstencil_dtype dtype, sparstencil_boundary bc,
@@ -174,7 +174,11 @@ sparstencil_status sparstencil_run_profiled(sparstencil_plan_t plan, const float
  * It calls no cudaMalloc, cudaFree or allocating library routine; the first call on a
  * device resolves the arrays' device addresses (cudaGetSymbolAddress) and should come
  * before any stream capture.  All calls share the arrays: each call clears what must
- * start at zero and re-uploads its tables, and calls that overlap on the GPU race. */
+ * start at zero and uploads the plan's tables from host memory (cudaMemcpyAsync on
+ * `stream`), and calls that overlap on the GPU race.  2D sparse plans only.  The plan
+ * runs at the depth sparstencil_query reports: a plan made with fusion_depth 0 that no
+ * sparstencil_run has tuned yet runs at its deepest planned depth (this entry point times
+ * no depths). */
 sparstencil_status sparstencil_run_noalloc(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
                                            cudaStream_t stream);
 
@@ -296,7 +300,8 @@ typedef struct {
   sparstencil_shape shape;
   int radius;
   const float* weights;      /* host cube as for sparstencil_plan, copied at submission */
-  int ndim;                  /* 2 or 3 */
+  int ndim;                  /* 2 or 3 (the server takes 2D and 3D jobs; 1D plans run through
+                                sparstencil_run) */
   const int64_t* dims;       /* copied at submission */
   sparstencil_dtype dtype;
   sparstencil_boundary bc;

@@ -170,11 +170,14 @@ std::vector<std::pair<int, int>> hierarchical_matching_nd(const std::vector<int>
 }
 
 // ---------------------------------------------------------------------------------------
-// Maximum-cardinality matching in a general graph (Edmonds' blossom algorithm, 1965): from
-// each free vertex grow an alternating tree by breadth-first search; an edge that closes an
-// odd cycle (a blossom) contracts the cycle onto its base, whose vertices all become outer
-// vertices of the tree; reaching a free vertex gives an augmenting path, which is flipped.
-// A greedy pass seeds the matching.  Returns mate[v] (-1: unmatched).
+// Maximum-cardinality matching in a general graph: Edmonds' blossom algorithm (J. Edmonds,
+// "Paths, trees, and flowers", Canadian J. Math. 17, 1965), in its common breadth-first
+// textbook formulation with a base array: from each free vertex grow an alternating tree by
+// breadth-first search; an edge that closes an odd cycle (a blossom) contracts the cycle
+// onto its base (the lowest common base of the edge's ends, found by marking the path from
+// one end to the root), whose vertices all become outer vertices of the tree; reaching a
+// free vertex gives an augmenting path, which is flipped.  A greedy pass seeds the
+// matching.  Returns mate[v] (-1: unmatched).
 // ---------------------------------------------------------------------------------------
 std::vector<int> max_cardinality_matching(const std::vector<std::vector<int>>& adj) {
   const int n = (int)adj.size();

@@ -65,14 +65,22 @@ def test_reference_arm_is_silent_on_other_ranks(capsys, monkeypatch):
 
 
 def test_profile_traffic_needs_the_profiled_depth():
-    """The roofline's `traffic` comes from the committed ncu summary only at the fused depth
+    """The roofline's `traffic` comes from a committed ncu summary only at the fused depth
     that summary captured (and only while the kernel sources match its sha)."""
     import re
     import bench
-    with open(os.path.join(ROOT, "profiles", "sweep2d_box9_4096.md")) as f:
-        text = f.read()
-    depth = int(re.search(r"fusion_depth:\s*([0-9]+)", text).group(1))
-    recorded = float(re.search(r"dram_bytes_per_launch_scaled:\s*([0-9.eE+]+)", text).group(1))
-    got = bench._profile_traffic(depth)
-    assert got is None or got == recorded
-    assert bench._profile_traffic(depth + 1) is None
+    prof_dir = os.path.join(ROOT, "profiles")
+    checked = 0
+    for name in sorted(os.listdir(prof_dir)):
+        with open(os.path.join(prof_dir, name)) as f:
+            text = f.read()
+        m_t = re.search(r"fusion_depth:\s*([0-9]+)", text)
+        m_b = re.search(r"dram_bytes_per_launch_scaled:\s*([0-9.eE+]+)", text)
+        if not (m_t and m_b):
+            continue
+        depth, recorded = int(m_t.group(1)), float(m_b.group(1))
+        got = bench._profile_traffic(depth, name)
+        assert got is None or got == recorded
+        assert bench._profile_traffic(depth + 1, name) is None
+        checked += 1
+    assert checked >= 1

@@ -1,7 +1,10 @@
 """GPU parity: the sparse tensor-core path (through the C ABI) against the FP64 oracle.
 
-Tolerances (rel-L2 over the whole grid, FP64, after the full run): single-word operands
-(FP16/BF16) 2e-3, split hi+lo operands 1e-5; the plain FP32 CUDA-core comparator 1e-5.
+Tolerances (FP64, after the full run): rel-L2 over the whole grid <= 2e-3 for single-word
+operands (FP16/BF16) and 1e-5 for split hi+lo operands; rel-Linf = max|x - ref| / max|ref|
+<= ten times that (2e-2 / 1e-4), so that a handful of wrong outputs fails even where it
+barely moves rel-L2; the plain FP32 CUDA-core comparator 1e-6 (rel-L2) and 1e-5 (rel-Linf).
+Sampled full-size cases apply the same bounds to the sampled points.
 """
 import numpy as np
 import pytest
@@ -11,6 +14,20 @@ from paper_2506_22969_gb300 import binding, inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp16": 2e-3, "bf16": 2e-3, "fp16_split": 1e-5, "bf16_split": 1e-5}
+LINF = {k: 10 * v for k, v in TOL.items()}
+
+
+def _rel(vals, ref):
+    """(rel-L2, rel-Linf) of sampled or whole-grid values against the oracle's."""
+    vals = np.asarray(vals, np.float64)
+    ref = np.asarray(ref, np.float64)
+    d = vals - ref
+    return (float(np.sqrt(np.sum(d * d) / np.sum(ref * ref))), float(np.max(np.abs(d)) / np.max(np.abs(ref))))
+
+
+def _assert_tol(l2, linf, dtype, *ctx):
+    assert l2 <= TOL[dtype], (dtype, l2, linf) + ctx
+    assert linf <= LINF[dtype], (dtype, l2, linf) + ctx
 
 
 @pytest.fixture(scope="module")
@@ -74,14 +91,13 @@ def test_sparse_matches_oracle(torch_cuda, oracle_mod, shape, r, recipe, dims, s
     got, _ = _run_sparse(torch_cuda, u, w, steps, dtype, bc, t, shape)
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
-    assert l2 <= TOL[dtype], (l2, linf)
+    _assert_tol(l2, linf, dtype)
     if bc == "dirichlet" and t > 1:
         # the frame the fused kernel cannot produce must meet the tolerance on its own
         bw = (t - 1) * r
         band = np.ones(dims, dtype=bool)
         band[bw:-bw, bw:-bw] = False
-        bl2 = np.sqrt(np.sum((got[band] - ref[band]) ** 2) / np.sum(ref[band] ** 2))
-        assert bl2 <= TOL[dtype], bl2
+        _assert_tol(*_rel(got[band], ref[band]), dtype, "band")
 
 
 def test_zero_and_one_step(torch_cuda, oracle_mod):
@@ -90,7 +106,7 @@ def test_zero_and_one_step(torch_cuda, oracle_mod):
     got0, _ = _run_sparse(torch_cuda, u, w, 0, "bf16", "periodic", 1, "box")
     np.testing.assert_array_equal(got0, u.astype(np.float64))
     got1, _ = _run_sparse(torch_cuda, u, w, 1, "bf16_split", "periodic", 1, "box")
-    assert oracle_mod.rel_errors(got1, oracle_mod.run(u, w, "periodic", 1))[0] <= 1e-5
+    _assert_tol(*oracle_mod.rel_errors(got1, oracle_mod.run(u, w, "periodic", 1)), "bf16_split")
 
 
 def test_autotuned_depth_matches_oracle(torch_cuda, oracle_mod):
@@ -110,7 +126,7 @@ def test_autotuned_depth_matches_oracle(torch_cuda, oracle_mod):
     assert binding.device_status() == 0
     assert torch.equal(y1, y2)
     ref = oracle_mod.run(u, w, "periodic", 20)
-    assert oracle_mod.rel_errors(y1.cpu().numpy().astype(np.float64), ref)[0] <= 1e-5
+    _assert_tol(*oracle_mod.rel_errors(y1.cpu().numpy().astype(np.float64), ref), "bf16_split")
 
 
 def test_closed_form_fourier_mode(torch_cuda):
@@ -129,8 +145,7 @@ def test_closed_form_fourier_mode(torch_cuda):
     u0 = 0.5 + 0.5 * np.cos(phase)
     ref = 0.5 * S ** T + 0.5 * np.real(lam ** T * np.exp(1j * phase))
     got, _ = _run_sparse(torch_cuda, u0, w, T, "bf16_split", "periodic", 1, "box")
-    err = np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2))
-    assert err <= 1e-5, err
+    _assert_tol(*_rel(got, ref), "bf16_split")
 
 
 def test_closed_form_sine_mode_dirichlet_fused(torch_cuda):
@@ -146,8 +161,7 @@ def test_closed_form_sine_mode_dirichlet_fused(torch_cuda):
     u32 = u0.astype(np.float32)
     ref = lam ** T * u32.astype(np.float64)
     got, _ = _run_sparse(torch_cuda, u32, w, T, "bf16_split", "dirichlet", 3, "star")
-    l2 = np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2))
-    assert l2 <= 1e-5, l2
+    _assert_tol(*_rel(got, ref), "bf16_split")
 
 
 def test_direct_fp32_matches_oracle(torch_cuda, oracle_mod):
@@ -161,7 +175,8 @@ def test_direct_fp32_matches_oracle(torch_cuda, oracle_mod):
         work = torch.empty_like(x)
         binding.direct_run(w, x, out, work, 9, bc=bc)
         ref = oracle_mod.run(u, w, bc, 9)
-        assert oracle_mod.rel_errors(out.cpu().numpy(), ref)[0] <= 1e-6
+        l2, linf = oracle_mod.rel_errors(out.cpu().numpy(), ref)
+        assert l2 <= 1e-6 and linf <= 1e-5, (shape, r, bc, l2, linf)
 
 
 def test_direct_fp32_3d(torch_cuda, oracle_mod):
@@ -172,7 +187,8 @@ def test_direct_fp32_3d(torch_cuda, oracle_mod):
     out, work = torch.empty_like(x), torch.empty_like(x)
     binding.direct_run(w, x, out, work, 5, bc="dirichlet")
     ref = oracle_mod.run(u, w, "dirichlet", 5)
-    assert oracle_mod.rel_errors(out.cpu().numpy(), ref)[0] <= 1e-6
+    l2, linf = oracle_mod.rel_errors(out.cpu().numpy(), ref)
+    assert l2 <= 1e-6 and linf <= 1e-5, (l2, linf)
 
 
 def test_error_norms_kernel(torch_cuda):
@@ -206,12 +222,11 @@ def test_full_size_box9_sampled(torch_cuda, oracle_mod):
     u = inputs.make_grid(cfg["grid"], cfg["seed"], cfg["dims"])
     rng = np.random.default_rng(0)
     pts = [tuple(int(v) for v in rng.integers(0, 4096, 2)) for _ in range(24)] + [(0, 0), (4095, 4095), (0, 4095)]
-    ref = np.array([oracle_mod.point(u, w, "periodic", cfg["steps"], p) for p in pts])
-    for dtype, tol in (("bf16", 2e-3), ("bf16_split", 1e-5)):
+    ref = oracle_mod.points(u, w, "periodic", cfg["steps"], pts)
+    for dtype in ("bf16", "bf16_split"):
         got, _ = _run_sparse(torch_cuda, u, w, cfg["steps"], dtype, "periodic", 1, "box")
         vals = np.array([got[p] for p in pts])
-        rel = np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2))
-        assert rel <= tol, (dtype, rel)
+        _assert_tol(*_rel(vals, ref), dtype)
 
 
 def test_bounded_wait_reports_timeout(torch_cuda):
@@ -305,7 +320,7 @@ def test_sparse_3d_matches_oracle(torch_cuda, oracle_mod, shape, recipe, dims, s
     got, _ = _run_sparse(torch_cuda, u, w, steps, dtype, bc, 1, shape)
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
-    assert l2 <= TOL[dtype], (l2, linf)
+    _assert_tol(l2, linf, dtype)
 
 
 def test_full_size_box3d27p_sampled(torch_cuda, oracle_mod):
@@ -317,28 +332,27 @@ def test_full_size_box3d27p_sampled(torch_cuda, oracle_mod):
     got, _ = _run_sparse(torch_cuda, u, w, cfg["steps"], "bf16_split", cfg["bc"], 1, cfg["shape"])
     rng = np.random.default_rng(2)
     pts = [tuple(int(rng.integers(0, d)) for d in cfg["dims"]) for _ in range(5)] + [(0, 0, 0), (255, 255, 255)]
-    ref = np.array([oracle_mod.point(u, w, cfg["bc"], cfg["steps"], p) for p in pts])
+    ref = oracle_mod.points(u, w, cfg["bc"], cfg["steps"], pts)
     vals = np.array([got[p] for p in pts])
-    assert np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2)) <= 1e-5
+    _assert_tol(*_rel(vals, ref), "bf16_split")
 
 
-@pytest.mark.parametrize("name,npts", [("star2d13p_8192", 3), ("box2d49p_8192", 2)])
+@pytest.mark.parametrize("name,npts", [("star2d13p_8192", 6), ("box2d49p_8192", 6)])
 def test_full_size_c4_sampled(torch_cuda, oracle_mod, name, npts):
     """Star-2D13P / Box-2D49P 8192^2, 200 steps, Gaussian weights, periodic, in the suite's
     launch configuration (autotuned fusion depth), single-word and split BF16: sampled points
-    against the dependence-cone oracle (a few seconds of FP64 work per point)."""
+    against the dependence-cone oracle (several seconds of FP64 work per point, on host threads)."""
     cfg = inputs.CONFIGS[name]
     w = inputs.stencil_weights(cfg["shape"], 2, cfg["radius"], cfg["recipe"], seed=cfg["seed"])
     u = inputs.make_grid(cfg["grid"], cfg["seed"], cfg["dims"])
     rng = np.random.default_rng(5)
-    pts = [tuple(int(rng.integers(0, d)) for d in cfg["dims"]) for _ in range(npts - 1)] + [(0, 8191)]
-    u64 = u.astype(np.float64)
-    ref = np.array([oracle_mod.point(u64, w, cfg["bc"], cfg["steps"], p) for p in pts])
+    pts = [tuple(int(rng.integers(0, d)) for d in cfg["dims"]) for _ in range(npts - 3)]
+    pts += [(0, 8191), (127, 128), (8191, 0)]  # grid corners and a tile corner
+    ref = oracle_mod.points(u, w, cfg["bc"], cfg["steps"], pts)
     for dtype in ("bf16", "bf16_split"):
         got, plan = _run_sparse(torch_cuda, u, w, cfg["steps"], dtype, cfg["bc"], 0, cfg["shape"])
         vals = np.array([got[p] for p in pts])
-        l2 = np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2))
-        assert l2 <= TOL[dtype], (dtype, plan.info().fusion_depth, l2)
+        _assert_tol(*_rel(vals, ref), dtype, plan.info().fusion_depth)
 
 
 def test_full_size_heat3d_sampled(torch_cuda, oracle_mod):
@@ -352,10 +366,9 @@ def test_full_size_heat3d_sampled(torch_cuda, oracle_mod):
     assert plan.info().low_accumulator == 1
     rng = np.random.default_rng(4)
     pts = [tuple(int(rng.integers(0, d)) for d in cfg["dims"]) for _ in range(6)] + [(0, 0, 0), (511, 0, 511)]
-    u64 = u.astype(np.float64)  # converted once, not per point
-    ref = np.array([oracle_mod.point(u64, w, cfg["bc"], cfg["steps"], p) for p in pts])
+    ref = oracle_mod.points(u, w, cfg["bc"], cfg["steps"], pts)
     vals = np.array([got[p] for p in pts])
-    assert np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2)) <= 1e-5
+    _assert_tol(*_rel(vals, ref), "fp16_split")
 
 
 @pytest.mark.parametrize("ndim,shape,dims,steps,bc,dtype,t", [
@@ -378,7 +391,7 @@ def test_low_accumulator_matches_oracle(torch_cuda, oracle_mod, ndim, shape, dim
     l2_one = oracle_mod.rel_errors(one, ref)[0]
     l2_two, linf_two = oracle_mod.rel_errors(two, ref)
     assert np.all(np.isfinite(two))
-    assert l2_two <= TOL[dtype], (l2_two, linf_two)
+    _assert_tol(l2_two, linf_two, dtype)
     assert l2_two <= 1.05 * l2_one, (l2_two, l2_one)
 
 
@@ -400,7 +413,7 @@ def test_dense_ablation_matches_oracle(torch_cuda, oracle_mod, ndim, shape, r, r
     assert plan.info().dense_ablation == 1
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
-    assert l2 <= TOL[dtype], (l2, linf)
+    _assert_tol(l2, linf, dtype)
 
 
 CASES_1D = [
@@ -427,7 +440,7 @@ def test_sparse_1d_matches_oracle(torch_cuda, oracle_mod, shape, r, recipe, leng
     assert plan.info().ndim == 1
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
-    assert l2 <= TOL[dtype], (l2, linf, plan.info().fusion_depth)
+    _assert_tol(l2, linf, dtype, plan.info().fusion_depth)
 
 
 def test_closed_form_fourier_mode_1d(torch_cuda):
@@ -442,7 +455,7 @@ def test_closed_form_fourier_mode_1d(torch_cuda):
     ref = 0.5 * float(np.sum(w)) ** T + 0.5 * np.real(lam ** T * np.exp(1j * th * x))
     got, plan = _run_sparse(torch_cuda, u0, w.astype(np.float32), T, "bf16_split", "periodic", 8, "box")
     assert plan.info().fusion_depth == 8
-    assert np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2)) <= 1e-5
+    _assert_tol(*_rel(got, ref), "bf16_split")
 
 
 @pytest.mark.parametrize("name", ["heat1d", "1d5p"])
@@ -455,10 +468,9 @@ def test_full_size_1d_sampled(torch_cuda, oracle_mod, name):
     u = inputs.make_grid(cfg["grid"], cfg["seed"], cfg["dims"])
     got, plan = _run_sparse(torch_cuda, u, w, cfg["steps"], "bf16_split", cfg["bc"], 0, cfg["shape"])
     pts = [(0,), (5120000,), (10239999,)]
-    u64 = u.astype(np.float64)
-    ref = np.array([oracle_mod.point(u64, w, cfg["bc"], cfg["steps"], p) for p in pts])
+    ref = oracle_mod.points(u, w, cfg["bc"], cfg["steps"], pts)
     vals = np.array([got[p] for p in pts])
-    assert np.sqrt(np.sum((vals - ref) ** 2) / np.sum(ref ** 2)) <= 1e-5, plan.info().fusion_depth
+    _assert_tol(*_rel(vals, ref), "bf16_split", plan.info().fusion_depth)
 
 
 def _custom(mask, seed):
@@ -488,7 +500,7 @@ def test_custom_mask_matches_oracle(torch_cuda, oracle_mod, name, dims, steps, b
     got, plan = _run_sparse(torch_cuda, u, w, steps, dtype, bc, t, "custom")
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
-    assert l2 <= TOL[dtype], (l2, linf, plan.info().pairing)
+    _assert_tol(l2, linf, dtype, plan.info().pairing)
 
 
 @pytest.mark.parametrize("ndim,dims,bc,t,steps", [
@@ -525,7 +537,7 @@ def test_degenerate_stencils(torch_cuda, oracle_mod, ndim, dims, bc, t, steps, d
         assert plan.info().fusion_depth == t
         l2, linf = oracle_mod.rel_errors(got, ref)
         assert np.all(np.isfinite(got))
-        assert l2 <= TOL[dtype], (np.argwhere(w).tolist(), l2, linf)
+        _assert_tol(l2, linf, dtype, np.argwhere(w).tolist())
 
 
 @pytest.mark.parametrize("ndim,shape,r,dims,steps,bc,dtype,t", [
@@ -547,4 +559,4 @@ def test_widest_stencils_match_oracle(torch_cuda, oracle_mod, ndim, shape, r, di
     assert plan.info().fusion_depth == t
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
-    assert l2 <= TOL[dtype], (l2, linf, plan.info().kpad)
+    _assert_tol(l2, linf, dtype, plan.info().kpad)
