@@ -320,8 +320,8 @@ def trace_case():
             c0 = ch[0, 0, 0]
             for kc in range(16):
                 if ch[0, kc, 0]:
-                    g = " | ".join(f"w{s}: start {ch[s, kc, 0] - c0:6d} loaded {ch[s, kc, 1] - c0:6d} "
-                                   f"free {ch[s, kc, 2] - c0:6d} pub {ch[s, kc, 3] - c0:6d}" for s in (0, 1))
+                    g = " | ".join(f"w{s}: start {ch[s, kc, 0] - c0:6d} free {ch[s, kc, 1] - c0:6d} "
+                                   f"stored {ch[s, kc, 2] - c0:6d} pub {ch[s, kc, 3] - c0:6d}" for s in (0, 1))
                     print(f"  tile 1 chunk {kc:2d}: {g} | mma ready {ch[2, kc, 0] - c0:6d} "
                           f"issued {ch[2, kc, 1] - c0:6d} (cycles)")
                     print("      stored  by gather warp: " + " ".join(f"{pub[1, w, kc] - c0:6d}" for w in range(16)))
@@ -437,20 +437,25 @@ def main():
     model = {}
 
     def autotune(dtype, wl=(cfg, w, x, y)):
+        """The layout search over fusion depth x 2D patch shape (16 x 8, 8 x 16), timed here
+        (the library's fusion_depth-0 search does the same on a plan's first run)."""
         c, ww, xx, yy = wl
         best = None
         tune.setdefault(c["name"], {})[dtype] = {}
         model.setdefault(c["name"], {})[dtype] = {}
         for t in candidates:
-            try:
-                pl = binding.Plan(ww, c["dims"], dtype=dtype, bc=c["bc"], fusion_depth=t, shape=c["shape"])
-            except binding.SparStencilError:
-                continue
-            ms = min(timed_runs(lambda: pl.run(xx, yy, c["steps"]), 2, 1))
-            tune[c["name"]][dtype][str(t)] = ms
-            model[c["name"]][dtype][str(t)] = pl.cost_model(t, *model_rates) * c["steps"] * 1e3
-            if best is None or ms < best[1]:
-                best = (t, ms, pl)
+            for r1 in (16, 8):
+                try:
+                    pl = binding.Plan(ww, c["dims"], dtype=dtype, bc=c["bc"], fusion_depth=t, shape=c["shape"],
+                                      layout=(r1, -1))
+                except binding.SparStencilError:
+                    continue
+                ms = min(timed_runs(lambda: pl.run(xx, yy, c["steps"]), 2, 1))
+                tune[c["name"]][dtype][f"t={t} patch={r1}x{128 // r1}"] = ms
+                if r1 == 16:
+                    model[c["name"]][dtype][str(t)] = pl.cost_model(t, *model_rates) * c["steps"] * 1e3
+                if best is None or ms < best[1]:
+                    best = (t, ms, pl)
         return best
 
     # clocks: sampled every 20 ms from the start of the fusion-depth search to the end of
@@ -564,7 +569,8 @@ def main():
             "config": {"workload": cfg["name"], "grid": [H, W], "steps_per_run": T, "boundary": cfg["bc"],
                        "stencil": "box 7x7 (49-point), Gaussian-decay weights (sigma 1.5) normalised to 1",
                        "precision": f"bf16_split ({info.mma_terms - 1} BF16 weight pieces, data hi+lo)",
-                       "fusion_depth": t_best, "crush": [info.r1, info.r2], "kpad": info.kpad,
+                       "fusion_depth": t_best, "crush": [info.r1, info.r2], "pairing": info.pairing,
+                       "kpad": info.kpad,
                        "mma_terms": info.mma_terms,
                        "l2_flush": "grids (2 x 256 MiB) larger than L2, plus a 512 MiB write before every timed run",
                        "parallelism": f"replicas x{world}"},

@@ -89,9 +89,10 @@ typedef struct {
  *            from 6 down to 1 in 2D, from 60 / radius in 1D and from 3 in 3D
  *            (Dirichlet fusion: 2D, radius <= 4), and the first sparstencil_run
  *            times two sweeps of every depth up to it (1D: of the powers of two below it and
- *            of the maximum) on its own input (after one warm-up
- *            sweep each; that call synchronises its stream once) and keeps the depth with the
- *            least time per step.  sparstencil_query reports the planned maximum until then.
+ *            of the maximum), for every candidate layout (see sparstencil_plan_set_layout), on
+ *            its own input (after one warm-up sweep each; that call synchronises its stream
+ *            once) and keeps the combination with the least time per step.
+ *            sparstencil_query reports the planned maximum depth until then.
  *   out_plan: receives the plan (owned by the library until sparstencil_plan_destroy).
  * Host only (no device work).  Errors: SPST_ERR_INVALID, SPST_ERR_UNSUPPORTED
  * (ndim not 1, 2 or 3, radius too large for TMEM, ...), SPST_ERR_NOMEM.
@@ -117,6 +118,22 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
  * SPST_ERR_UNSUPPORTED (the plan's fusion depth does not fit in TMEM this way; the plan is
  * left unchanged).  Host only. */
 sparstencil_status sparstencil_plan_set_low_accumulator(sparstencil_plan_t plan, int enable);
+
+/* Fixes the plan's layout instead of leaving it to the search of a fusion_depth-0 plan:
+ *   r1:      2D patch shape, 16 (16 x 8 outputs per patch, 8 patches across a 128 x 128 tile,
+ *            the default) or 8 (8 x 16, 16 across); 1D and 3D plans accept only their own r1
+ *            (128 and 8)
+ *   pairing: column pairing of the 2:4 conversion (Sec. 3.2): 0 = Algorithm 1, 1 = a maximum
+ *            matching on the stencil's actual support (stars, custom masks), -1 = whichever
+ *            needs fewer K chunks (the default)
+ * A plan made with fusion_depth 0 otherwise times, at its first run, every depth of its search
+ * with both 2D patch shapes and, for supports smaller than their box, both pairings, and keeps
+ * the fastest combination (the layout search of Sec. 3.3, Eq. 11, done by measurement);
+ * sparstencil_query reports the choice (r1, r2, pairing).  Must be called before the plan's
+ * first run.  Errors: SPST_ERR_INVALID (null plan, bad pairing, plan already ran),
+ * SPST_ERR_UNSUPPORTED (other r1, or the layout does not fit; the plan is left unchanged).
+ * Host only. */
+sparstencil_status sparstencil_plan_set_layout(sparstencil_plan_t plan, int r1, int pairing);
 
 /* The dense-versus-sparse ablation: enable != 0 runs the same morphed, permuted A' (Sec. 3.1-3.2)
  * as dense tcgen05 MMAs (kind::f16, K = 16 per instruction, the 2:4 zeros stored explicitly in
@@ -194,13 +211,21 @@ sparstencil_status sparstencil_bind_workspace(sparstencil_plan_t plan, void* dev
                                               cudaStream_t stream);
 
 /* Runs n independent jobs (plans[i] on in[i] -> out[i] for steps[i] steps) as one CUDA
- * graph launched on `stream`: job i's copy-in and sweeps form branch i mod 16 of the graph,
- * and the branches run side by side on the device (many small grids share the SMs).  Plans
- * must be distinct.  Before capturing, the call prepares every plan (workspace, the
- * fusion-depth search of fusion_depth-0 plans, device tables) and synchronises `stream`;
- * the graph itself is launched asynchronously.  Results equal those of sparstencil_run on
- * each job (same plans, same kernels).  Errors as sparstencil_run, plus SPST_ERR_INVALID
- * for repeated plans. */
+ * graph launched on `stream`: the jobs' copy-ins, then for each sweep index s one persistent
+ * launch of the multi-grid sweep kernel over every job that has a sweep s (per kernel
+ * template: FP16 or BF16, single or split words, dimensionality; at most 64 jobs per
+ * launch).  The launch shares the SMs out by tile count, at least one CTA per job; a CTA
+ * works on one job's tiles with that job's tables and tensor map, so many small grids share
+ * the GPU in each launch.  Dirichlet bands and periodic ghost refreshes of the jobs that
+ * need them follow each launch.  Plans must be distinct.  The first call for a set of jobs prepares every plan (workspace, the
+ * fusion-depth search of fusion_depth-0 plans, device tables), synchronises `stream`,
+ * captures and instantiates the graph and launches it.  The library keeps the instantiated
+ * graph (up to 16 of them, least recently used dropped first): a later call with the same
+ * plans in the same state (workspace, fusion depth), the same grids and the same step counts
+ * only launches it, asynchronously and without synchronising.  Destroying a plan or binding
+ * it a new workspace drops the graphs that use it.  Results equal those of sparstencil_run
+ * on each job (same plans, same kernels).  Errors as sparstencil_run, plus
+ * SPST_ERR_INVALID for repeated plans. */
 sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const float* const* in,
                                          float* const* out, const int64_t* steps, int n, cudaStream_t stream);
 
@@ -277,7 +302,7 @@ sparstencil_status sparstencil_trace(int enable);
 /* Copies up to n trace entries to host memory; synchronous.  Entries 0..511: layout
  * [role][tile][start, end] (4 x 64 x 2, nanoseconds); entries 512..703: clock64 stamps of
  * the K chunks of CTA 0's second tile, [source][chunk < 16][4]: sources 0 and 1 the first and
- * the last B'' gather warp (chunk start, halo values loaded, chunk slot free, chunk
+ * the last B'' gather warp (chunk start, chunk slot free, stores issued, chunk
  * published), source 2 the MMA issuer (chunk complete in shared memory, MMAs issued);
  * entries 704..959: [gather warp < 16][chunk < 16] publish stamps of the same tile;
  * entries 960..1215: the same warps' stamps just before the chunk's proxy fence. */

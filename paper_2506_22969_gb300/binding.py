@@ -59,7 +59,7 @@ class ServerSummary(ctypes.Structure):
                 ("max_s", ctypes.c_double), ("peak_bytes", ctypes.c_size_t), ("gstencil_per_s", ctypes.c_double)]
 
 
-EXPORTS = ["sparstencil_plan", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host",
+EXPORTS = ["sparstencil_plan", "sparstencil_plan_set_layout", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host",
            "sparstencil_run_noalloc", "sparstencil_plan_destroy",
            "sparstencil_workspace_bytes", "sparstencil_bind_workspace", "sparstencil_run_batch", "sparstencil_query",
            "sparstencil_plan_tables", "sparstencil_table_kpad", "sparstencil_direct_run", "sparstencil_error_norms",
@@ -90,6 +90,7 @@ def load():
     lib.sparstencil_plan_destroy.argtypes = [vp]
     lib.sparstencil_plan_set_low_accumulator.argtypes = [vp, i32]
     lib.sparstencil_plan_set_dense_ablation.argtypes = [vp, i32]
+    lib.sparstencil_plan_set_layout.argtypes = [vp, i32, i32]
     lib.sparstencil_cost_model.argtypes = [vp, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_double)]
     lib.sparstencil_workspace_bytes.argtypes = [vp]
@@ -153,7 +154,7 @@ class Plan:
     """A planned stencil (sparstencil_plan); destroys itself when garbage-collected."""
 
     def __init__(self, weights, dims, dtype="bf16", bc="periodic", fusion_depth=1, shape="box",
-                 low_accumulator=None, dense=False):
+                 low_accumulator=None, dense=False, layout=None):
         lib = load()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
         self.ndim = w.ndim
@@ -171,6 +172,8 @@ class Plan:
             self.set_low_accumulator(bool(low_accumulator))
         if dense:
             self.set_dense_ablation(True)
+        if layout is not None:  # (r1, pairing); None: the library's default or search
+            self.set_layout(*layout)
 
     def cost_model(self, depth, tensor_flops, hbm_bytes_per_s, smem_bytes_per_s) -> float:
         """sparstencil_cost_model: the Sec. 3.3 model's seconds per time step at this depth."""
@@ -183,6 +186,11 @@ class Plan:
         """sparstencil_plan_set_dense_ablation: dense tcgen05 MMAs on the uncompressed A'
         (before the first run)."""
         _check(load().sparstencil_plan_set_dense_ablation(self._h, 1 if enable else 0))
+
+    def set_layout(self, r1, pairing=-1):
+        """sparstencil_plan_set_layout: 2D patch shape (r1 = 16: 16 x 8, r1 = 8: 8 x 16) and
+        column pairing (0 Algorithm 1, 1 maximum matching, -1 fewer chunks), before the first run."""
+        _check(load().sparstencil_plan_set_layout(self._h, int(r1), int(pairing)))
 
     def set_low_accumulator(self, enable=True):
         """sparstencil_plan_set_low_accumulator: split terms after A_hi B_hi go to a TMEM

@@ -189,6 +189,196 @@ __global__ void __launch_bounds__(256) direct2d_kernel(const __grid_constant__ D
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Register-marching comparators for grids whose width is a multiple of 4 (every float4 row
+// access aligned).  A warp owns 128 consecutive columns (a float4 per lane) and walks the
+// input rows (2D) or planes (3D, radius 1) of its segment once, in order.  Each input row's
+// 4 + 2R values per lane (its float4; R halo values from each neighbouring lane by shuffle,
+// or from global memory at the warp's edges) are added into the 2R+1 outputs that use them,
+// which wait in registers; an output is stored (float4) once its last input has been added.
+// Per output the FMAs run in lexicographic offset order ((dy, dx) in 2D, (dz, dy, dx) in
+// 3D), zero weights of the dense cube included (an FMA with weight 0 leaves a finite sum
+// unchanged); the weights are operands from the kernel's constant parameters.
+// ---------------------------------------------------------------------------------------
+constexpr int DSEG = 64;   // 2D: most output rows per warp (fewer when the grid has few columns)
+constexpr int D3SEG = 32;  // 3D: output planes per warp
+constexpr int DWARPS = 4;  // warps per CTA
+
+__device__ __forceinline__ float f4c(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+
+// The 4 + 2R values of one input row around the lane's four columns x .. x+3: s[R + j] is
+// column x + j (j = -R .. 3 + R).  row: the row's first element, or null for a row of zeros.
+template <int R>
+__device__ __forceinline__ void row_window(const float* __restrict__ row, int64_t x, bool active, bool left_shfl,
+                                           bool right_shfl, int64_t xl, int64_t xr, float (&s)[4 + 2 * R]) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f), hl = v, hr = v;
+  if (row && active) {
+    v = *reinterpret_cast<const float4*>(row + x);
+    if (!left_shfl && xl >= 0) hl = *reinterpret_cast<const float4*>(row + xl);
+    if (!right_shfl && xr >= 0) hr = *reinterpret_cast<const float4*>(row + xr);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; j++) s[R + j] = f4c(v, j);
+#pragma unroll
+  for (int m = 0; m < R; m++) {
+    const float up = __shfl_up_sync(0xffffffffu, f4c(v, 3 - m), 1);
+    const float dn = __shfl_down_sync(0xffffffffu, f4c(v, m), 1);
+    s[R - 1 - m] = left_shfl ? up : f4c(hl, 3 - m);
+    s[R + 4 + m] = right_shfl ? dn : f4c(hr, m);
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(DWARPS * 32) direct2d_reg_kernel(const __grid_constant__ DirectParams p,
+                                                                    const float* __restrict__ in,
+                                                                    float* __restrict__ out, int seg) {
+  constexpr int K = 2 * R + 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t H = p.H, W = p.W;
+  const int64_t xw = ((int64_t)blockIdx.x * DWARPS + (threadIdx.x >> 5)) * 128;
+  if (xw >= W) return;  // the whole warp
+  const int64_t x = xw + 4 * lane;
+  const bool active = x < W;
+  const int64_t y0 = (int64_t)blockIdx.y * seg;
+  // halo columns: from lane l-1 / l+1 inside the warp and the grid, else one float4 column
+  // (wrapped when periodic; -1: outside a Dirichlet grid, zeros)
+  const bool left_shfl = lane > 0, right_shfl = lane < 31 && x + 4 < W;
+  const int64_t xl = x - 4 >= 0 ? x - 4 : (p.periodic ? W - 4 : -1);
+  const int64_t xr = x + 4 < W ? x + 4 : (p.periodic ? 0 : -1);
+  float acc[K][4];
+#pragma unroll
+  for (int k = 0; k < K; k++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[k][j] = 0.f;
+  // input rows y0 - R .. y0 + nout + R - 1: each wraps at most once (H >= R)
+  const int nout = (int)(H - y0 < seg ? H - y0 : seg);
+  const int nrows = nout + 2 * R;
+  for (int ib = 0; ib < nrows; ib += K) {
+#pragma unroll
+    for (int ii = 0; ii < K; ii++) {
+      const int i = ib + ii;  // input row y0 - R + i
+      if (i >= nrows) break;
+      int64_t r = y0 - R + i;
+      const float* row = nullptr;
+      if (p.periodic) {
+        r = r < 0 ? r + H : (r >= H ? r - H : r);
+        row = in + r * W;
+      } else if (r >= 0 && r < H) {
+        row = in + r * W;
+      }
+      float s[4 + 2 * R];
+      row_window<R>(row, x, active, left_shfl, right_shfl, xl, xr, s);
+      // output row y0 + i - R - a takes this row through weight row a (a = -R .. R); its
+      // accumulator slot is (i - R - a) mod K (compile-time: ib is a multiple of K)
+#pragma unroll
+      for (int a = -R; a <= R; a++) {
+        const int slot = ((ii - R - a) % K + 2 * K) % K;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+          for (int b = -R; b <= R; b++)
+            acc[slot][j] = fmaf(p.wdense[(a + R) * K + (b + R)], s[R + j + b], acc[slot][j]);
+      }
+      // output row y0 + i - 2R has now taken its last input row
+      const int done = ((ii - 2 * R) % K + 2 * K) % K;
+      const int oy = i - 2 * R;
+      if (oy >= 0 && active)
+        *reinterpret_cast<float4*>(out + (y0 + oy) * W + x) =
+            make_float4(acc[done][0], acc[done][1], acc[done][2], acc[done][3]);
+#pragma unroll
+      for (int j = 0; j < 4; j++) acc[done][j] = 0.f;
+    }
+  }
+}
+
+// 3D, radius 1: warp w of the CTA owns rows y .. y + D3ROWS - 1 (y = (blockIdx.y * DWARPS +
+// w) * D3ROWS) and 128 columns; it walks the D3SEG + 2 input planes of its z segment, taking
+// rows y-1 .. y+D3ROWS of each.  STAR: only the 7 points of the star (the other weights are
+// zero), in the same order; two rows per warp (the dense cube keeps one, for registers).
+template <bool STAR, int D3ROWS = STAR ? 2 : 1>
+__global__ void __launch_bounds__(DWARPS * 32) direct3d_reg_kernel(const __grid_constant__ DirectParams p,
+                                                                    const float* __restrict__ in,
+                                                                    float* __restrict__ out) {
+  constexpr int NR = D3ROWS + 2;  // input rows per plane
+  const int lane = threadIdx.x & 31;
+  const int64_t D = p.D, H = p.H, W = p.W;
+  const int64_t xw = (int64_t)blockIdx.x * 128;
+  const int64_t y = ((int64_t)blockIdx.y * DWARPS + (threadIdx.x >> 5)) * D3ROWS;
+  if (y >= H) return;  // the whole warp
+  const int64_t x = xw + 4 * lane;
+  const bool active = x < W;
+  const int64_t z0 = (int64_t)blockIdx.z * D3SEG;
+  const bool left_shfl = lane > 0, right_shfl = lane < 31 && x + 4 < W;
+  const int64_t xl = x - 4 >= 0 ? x - 4 : (p.periodic ? W - 4 : -1);
+  const int64_t xr = x + 4 < W ? x + 4 : (p.periodic ? 0 : -1);
+  // input row d of a plane is y - 1 + d (wrapped once when periodic: H >= 1 and
+  // y + D3ROWS <= H + D3ROWS - 1); rows past the grid's end, or outside a Dirichlet grid, read zeros
+  int64_t ys[NR];
+  bool yin[NR];
+#pragma unroll
+  for (int d = 0; d < NR; d++) {
+    int64_t yy = y + d - 1;
+    yin[d] = p.periodic || (yy >= 0 && yy < H);
+    while (yy < 0) yy += H;
+    while (yy >= H) yy -= H;
+    ys[d] = yy;
+  }
+  float acc[3][D3ROWS][4];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int r = 0; r < D3ROWS; r++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) acc[k][r][j] = 0.f;
+  // input planes z0 - 1 .. z0 + nout: each wraps at most once
+  const int nout = (int)(D - z0 < D3SEG ? D - z0 : D3SEG);
+  const int npl = nout + 2;
+  for (int ib = 0; ib < npl; ib += 3) {
+#pragma unroll
+    for (int ii = 0; ii < 3; ii++) {
+      const int i = ib + ii;  // input plane z0 - 1 + i
+      if (i >= npl) break;
+      int64_t z = z0 - 1 + i;
+      bool zin = true;
+      if (p.periodic)
+        z = z < 0 ? z + D : (z >= D ? z - D : z);
+      else
+        zin = z >= 0 && z < D;
+      float s[NR][6];
+#pragma unroll
+      for (int d = 0; d < NR; d++)
+        row_window<1>((zin && yin[d]) ? in + (z * H + ys[d]) * W : nullptr, x, active, left_shfl, right_shfl, xl,
+                      xr, s[d]);
+#pragma unroll
+      for (int a = -1; a <= 1; a++) {
+        const int slot = ((ii - 1 - a) % 3 + 6) % 3;
+#pragma unroll
+        for (int r = 0; r < D3ROWS; r++)
+#pragma unroll
+          for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+              for (int dx = 0; dx < 3; dx++) {
+                const int nz = (a != 0 ? 1 : 0) + (dy != 1 ? 1 : 0) + (dx != 1 ? 1 : 0);
+                if (STAR && nz > 1) continue;
+                acc[slot][r][j] = fmaf(p.wdense[((a + 1) * 3 + dy) * 3 + dx], s[r + dy][j + dx], acc[slot][r][j]);
+              }
+      }
+      const int done = ((ii - 2) % 3 + 3) % 3;
+      const int oz = i - 2;
+#pragma unroll
+      for (int r = 0; r < D3ROWS; r++) {
+        if (oz >= 0 && active && y + r < H)
+          *reinterpret_cast<float4*>(out + ((z0 + oz) * H + y + r) * W + x) =
+              make_float4(acc[done][r][0], acc[done][r][1], acc[done][r][2], acc[done][r][3]);
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[done][r][j] = 0.f;
+      }
+    }
+  }
+}
+
 // 1D: a CTA covers 2048 outputs; each thread computes 8 of them, 256 apart (coalesced), in
 // the fixed offset order.
 constexpr int E1X = 2048;
@@ -521,6 +711,16 @@ cudaError_t launch_pad_copy2d(const float* in, float* padded, int H, int W, int 
 
 template <int R>
 static cudaError_t launch_direct2d(const DirectParams& p, const float* in, float* out, cudaStream_t stream) {
+  if (p.W % 4 == 0) {
+    // rows per warp: DSEG, fewer when the grid has too few warps for the SMs (about 48 warps
+    // per SM); a shorter segment re-reads 2R more rows per segment, mostly from L2
+    const int64_t col_warps = (p.W + 127) / 128;
+    int64_t seg = DSEG;
+    while (seg > 8 && col_warps * ((p.H + seg - 1) / seg) < 152 * 48) seg /= 2;
+    dim3 g((unsigned)((p.W + 128 * DWARPS - 1) / (128 * DWARPS)), (unsigned)((p.H + seg - 1) / seg));
+    direct2d_reg_kernel<R><<<g, DWARPS * 32, 0, stream>>>(p, in, out, (int)seg);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((p.W + DTX - 1) / DTX), (unsigned)((p.H + DTY - 1) / DTY));
   const size_t smem = (size_t)(DTX + 2 * R) * (DTY + 2 * R) * sizeof(float);
   if (smem > 48 * 1024) {
@@ -580,6 +780,21 @@ cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* ou
       case 4: return launch_direct2d<4>(p, in, out, stream);
       default: return cudaErrorInvalidValue;
     }
+  }
+  if (r == 1 && p.W % 4 == 0) {
+    bool star = true;  // only the centre and the six axis neighbours are nonzero
+    for (int idx = 0; idx < 27; idx++) {
+      const int a = idx / 9, b = (idx / 3) % 3, c = idx % 3;
+      if ((a != 1) + (b != 1) + (c != 1) > 1 && p.wdense[idx] != 0.f) star = false;
+    }
+    const int rows = star ? 2 : 1;  // output rows per warp (the kernels' D3ROWS)
+    dim3 g((unsigned)((p.W + 127) / 128), (unsigned)((p.H + DWARPS * rows - 1) / (DWARPS * rows)),
+           (unsigned)((p.D + D3SEG - 1) / D3SEG));
+    if (star)
+      direct3d_reg_kernel<true><<<g, DWARPS * 32, 0, stream>>>(p, in, out);
+    else
+      direct3d_reg_kernel<false><<<g, DWARPS * 32, 0, stream>>>(p, in, out);
+    return cudaGetLastError();
   }
   if (r == 1) {
     dim3 grid((unsigned)((p.W + E3X - 1) / E3X), (unsigned)((p.H + E3Y - 1) / E3Y), (unsigned)((p.D + E3Z - 1) / E3Z));

@@ -4,7 +4,10 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <list>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -103,7 +106,12 @@ spst::Word word_of(sparstencil_dtype d) {
 
 }  // namespace
 
+namespace {
+std::atomic<uint64_t> g_plan_uid{1};
+}
+
 struct sparstencil_plan_s {
+  uint64_t uid = g_plan_uid.fetch_add(1);  // never reused (keys the batch graph cache)
   sparstencil_shape shape;
   int ndim = 2, radius = 1;
   sparstencil_dtype dtype;
@@ -111,7 +119,9 @@ struct sparstencil_plan_s {
   int requested_t = 1, t = 1, t_max = 1;
   bool lo_acc = false;  // split operands: low-order MMA terms in an accumulator of their own
   bool dense = false;   // the dense-MMA ablation (uncompressed A', dense tcgen05 MMAs)
-  bool autotune_pending = false;  // fusion_depth 0: t is chosen by timing at the first run
+  bool autotune_pending = false;  // fusion_depth 0: t (and the layout) chosen by timing at the first run
+  spst::Pairing pairing_pref = spst::Pairing::Auto;  // column pairing of the 2:4 conversion
+  bool layout_fixed = false;  // set by sparstencil_plan_set_layout: the search keeps this layout
   std::vector<double> w64;  // input weights (FP32 values promoted exactly)
   PlanGeometry geo;
   SweepTables full;
@@ -158,10 +168,10 @@ std::mutex g_table_cache_mu;
 std::map<std::string, SweepTables> g_table_cache;
 
 std::string tables_cached(const std::vector<double>& wf, int R, const PlanGeometry& geo, spst::Word word, int pieces,
-                          SweepTables* out) {
+                          SweepTables* out, spst::Pairing pairing) {
   std::string key;
   auto put = [&](const void* q, size_t n) { key.append((const char*)q, n); };
-  const int ints[6] = {R, geo.ndim, geo.P, geo.box_h, geo.G, pieces};
+  const int ints[8] = {R, geo.ndim, geo.P, geo.box_h, geo.G, pieces, geo.r1, (int)pairing};
   put(ints, sizeof(ints));
   put(&word, sizeof(word));
   put(wf.data(), wf.size() * sizeof(double));
@@ -173,7 +183,7 @@ std::string tables_cached(const std::vector<double>& wf, int R, const PlanGeomet
       return "";
     }
   }
-  std::string err = spst::build_sweep_tables_2d(wf, R, geo, word, pieces, true, out);
+  std::string err = spst::build_sweep_tables_2d(wf, R, geo, word, pieces, true, out, pairing);
   if (!err.empty()) return err;
   std::lock_guard<std::mutex> lock(g_table_cache_mu);
   if (g_table_cache.size() >= kTableCacheMax) g_table_cache.clear();
@@ -183,10 +193,10 @@ std::string tables_cached(const std::vector<double>& wf, int R, const PlanGeomet
 
 // Inputs one patch's outputs read through the composed stencil wf of radius R (the nonzero
 // columns of A', a lower bound on K_pad): |patch + support(wf)|, counted on a bitmap.
-int64_t patch_inputs(const std::vector<double>& wf, int ndim, int R) {
+int64_t patch_inputs(const std::vector<double>& wf, int ndim, int R, const PlanGeometry& geo) {
   const int kt = 2 * R + 1;
-  const int r1 = ndim == 1 ? Tile1D::R1 : ndim == 2 ? Tile2D::R1 : Tile3D::R1;
-  const int r2 = ndim == 1 ? 1 : ndim == 2 ? Tile2D::R2 : Tile3D::R2;
+  const int r1 = ndim == 1 ? Tile1D::R1 : ndim == 2 ? geo.r1 : Tile3D::R1;
+  const int r2 = ndim == 1 ? 1 : ndim == 2 ? geo.r2 : Tile3D::R2;
   const int r3 = ndim == 3 ? Tile3D::R3 : 1;
   const int kz = ndim == 3 ? kt : 1, ky = ndim >= 2 ? kt : 1;
   const int bx = r1 + kt - 1, by = r2 + ky - 1, bz = r3 + kz - 1;
@@ -210,7 +220,7 @@ std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
     // cheap rejection before the matching: even with the fewest pieces (two) and no zero
     // columns, K_pad >= the patch's input count, and the A'' pieces, metadata and one
     // accumulator must fit the 512 TMEM columns
-    const int64_t kmin = (patch_inputs(wf, p->ndim, depth * p->radius) + 31) / 32 * 32;
+    const int64_t kmin = (patch_inputs(wf, p->ndim, depth * p->radius, p->geo) + 31) / 32 * 32;
     const int64_t need = (p->dense ? 2 * (kmin / 2) : 2 * (kmin / 4) + 8 * ((kmin / 32 + 1) / 2)) +
                          (p->lo_acc ? 256 : 128);
     if (need > 512) return std::string("stencil too wide for TMEM (kpad >= ") + std::to_string(kmin) + ")";
@@ -228,13 +238,13 @@ std::string build_tables(sparstencil_plan_t p, int depth, SweepTables* out) {
   // ablation's uncompressed A' takes twice the columns; in every case two pieces replace three
   // when they leave room for more tile buffers.
   const int pieces = (is_split(p->dtype) && word_of(p->dtype) == spst::Word::BF16) ? 3 : 2;
-  std::string err = tables_cached(wf, depth * p->radius, p->geo, word_of(p->dtype), pieces, out);
+  std::string err = tables_cached(wf, depth * p->radius, p->geo, word_of(p->dtype), pieces, out, p->pairing_pref);
   if (!err.empty()) return err;
   const int buffers3 = tmem_accumulators(*out, p->lo_acc, p->dense);
   const bool retry = buffers3 == 0 || (!p->lo_acc && depth >= 2 && buffers3 < 2);
   if (pieces == 3 && retry) {
     SweepTables two;
-    err = tables_cached(wf, depth * p->radius, p->geo, word_of(p->dtype), 2, &two);
+    err = tables_cached(wf, depth * p->radius, p->geo, word_of(p->dtype), 2, &two, p->pairing_pref);
     if (!err.empty()) return err;
     if (tmem_accumulators(two, p->lo_acc, p->dense) > tmem_accumulators(*out, p->lo_acc, p->dense))
       *out = std::move(two);
@@ -302,7 +312,8 @@ const SweepTables* tables_for(sparstencil_plan_t p, int depth, std::string* err)
 // call returns).
 sparstencil_status ensure_device_tables(sparstencil_plan_t p, int depth, const SweepTables& T, DeviceTables** out,
                                         cudaStream_t stream) {
-  auto& dt = p->dev_tables[depth];
+  // keyed by depth and layout (patch shape, pairing): the fusion-depth search times several
+  auto& dt = p->dev_tables[depth * 8 + (p->geo.r1 == 8 ? 4 : 0) + ((int)p->pairing_pref + 1)];
   if (!dt.lut) {
     const std::vector<uint32_t> dense_words = p->dense ? spst::dense_a_words(T, word_of(p->dtype)) : std::vector<uint32_t>();
     const std::vector<uint32_t>& aw = p->dense ? dense_words : T.a_words;
@@ -443,6 +454,7 @@ spst::Sweep2DParams sweep_params(sparstencil_plan_t p, const SweepTables& T, con
   prm.D = (int)g.D;
   prm.dim3 = g.ndim == 3 ? 1 : 0;
   prm.dim1 = g.ndim == 1 ? 1 : 0;
+  prm.tall = (g.ndim == 2 && g.r1 == 8) ? 1 : 0;
   prm.G = g.G;
   prm.tiles_x = (int)g.tiles_x;
   prm.tiles_y = (int)g.tiles_y;
@@ -545,18 +557,79 @@ std::vector<int> autotune_depths(const sparstencil_plan_s* p) {
   return d;
 }
 
+// A layout of the sweep tables: the 2D patch shape (r1 = 16: 16 x 8, r1 = 8: 8 x 16) and the
+// column pairing of the 2:4 conversion.
+struct Layout {
+  int r1;
+  spst::Pairing pairing;
+};
+
+// Switches the plan's tables to layout L: the full sweep's tables are rebuilt (from the
+// process-wide cache when another plan built them), remainder tables are dropped (rebuilt on
+// demand); device tables are keyed by layout and stay.  Returns "" or the planner's reason.
+std::string apply_layout(sparstencil_plan_t p, const Layout& L) {
+  const PlanGeometry old_geo = p->geo;
+  const spst::Pairing old_pairing = p->pairing_pref;
+  if (p->geo.ndim == 2) {
+    p->geo.r1 = L.r1;
+    p->geo.r2 = 128 / L.r1;
+  }
+  p->pairing_pref = L.pairing;
+  SweepTables T;
+  const std::string err = build_tables(p, p->t, &T);
+  if (!err.empty()) {
+    p->geo = old_geo;
+    p->pairing_pref = old_pairing;
+    return err;
+  }
+  p->full = std::move(T);
+  p->rem.clear();
+  return "";
+}
+
+// The layouts the first run of an autotuned plan times: both 2D patch shapes, and for a
+// support smaller than its box (stars, custom masks) both pairings where they differ.
+std::vector<Layout> autotune_layouts(sparstencil_plan_t p) {
+  std::vector<Layout> out;
+  if (p->layout_fixed) return {Layout{p->geo.r1, p->pairing_pref}};
+  const std::vector<int> shapes = p->geo.ndim == 2 ? std::vector<int>{16, 8} : std::vector<int>{p->geo.r1};
+  for (int r1 : shapes) {
+    Layout a{r1, spst::Pairing::Algorithm1}, m{r1, spst::Pairing::Matching};
+    if (!apply_layout(p, a).empty()) continue;
+    const int a_pairing = p->full.pairing;
+    out.push_back(a);
+    if (apply_layout(p, m).empty() && p->full.pairing != a_pairing) out.push_back(m);
+  }
+  return out;
+}
+
+// The layout search of Sec. 3.3 (Eq. 11, the argmin over the candidate layouts), done by
+// measurement for a plan made with fusion_depth 0: copies `in` into the padded grid and, for
+// every candidate layout (patch shape, pairing) and fusion depth, times two sweeps after one
+// warm-up sweep; keeps the candidate with the least time per time step.  Synchronises the
+// stream; the caller's run then starts from a fresh copy-in.
 sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStream_t stream) {
   int* status = spst::device_status_word();
   if (!status) return fail(SPST_ERR_CUDA, "device status word unavailable");
-  // every depth's tables are uploaded ahead of the copy-in kernel, so that no copy sits
-  // between two sweeps (a sweep's set-up may overlap the kernel before it)
+  const Layout start{p->geo.r1, p->pairing_pref};
+  const std::vector<Layout> layouts = autotune_layouts(p);
+  if (layouts.empty()) {
+    apply_layout(p, start);
+    p->autotune_pending = false;
+    return SPST_OK;
+  }
   const std::vector<int> depths = autotune_depths(p);
-  for (int depth : depths) {
-    std::string err;
-    const SweepTables* T = tables_for(p, depth, &err);
-    DeviceTables* dt = nullptr;
-    sparstencil_status su = T ? ensure_device_tables(p, depth, *T, &dt, stream) : SPST_OK;
-    if (su != SPST_OK) return su;
+  // every candidate's tables are uploaded ahead of the copy-in kernel, so that no copy sits
+  // between two sweeps (a sweep's set-up may overlap the kernel before it)
+  for (const Layout& L : layouts) {
+    if (!apply_layout(p, L).empty()) continue;
+    for (int depth : depths) {
+      std::string err;
+      const SweepTables* T = tables_for(p, depth, &err);
+      DeviceTables* dt = nullptr;
+      sparstencil_status su = T ? ensure_device_tables(p, depth, *T, &dt, stream) : SPST_OK;
+      if (su != SPST_OK) return su;
+    }
   }
   SPST_CUDA(copy_in(p, in, p->pad(0), 3 * p->t_max, stream, p->maxabs), "pad copy");
   cudaEvent_t e0, e1;
@@ -565,52 +638,58 @@ sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStr
     cudaEventDestroy(e0);
     return fail(SPST_ERR_CUDA, "cudaEventCreate");
   }
-  int best = p->t;
+  int best_t = p->t;
+  Layout best_l = layouts[0];
   double best_ms = 1e300;
   sparstencil_status s = SPST_OK;
-  for (size_t di = 0; di < depths.size() && s == SPST_OK; di++) {
-    const int depth = depths[di];
-    std::string err;
-    const SweepTables* T = tables_for(p, depth, &err);
-    if (!T) continue;
-    DeviceTables* dt = nullptr;
-    if ((s = ensure_device_tables(p, depth, *T, &dt, stream)) != SPST_OK) break;
-    int cur = 0;
-    float ms = 0.f;
-    for (int k = 0; k < 3 && s == SPST_OK; k++) {
-      if (k == 1 && cudaEventRecord(e0, stream) != cudaSuccess) s = fail(SPST_ERR_CUDA, "cudaEventRecord");
-      spst::Sweep2DParams prm = sweep_params(p, *T, *dt, status);
-      set_output(p, &prm, p->pad(1 - cur), nullptr, false);
-      if (spst::launch_sweep2d(p->tmap[cur], prm, p->num_sms, stream) != cudaSuccess ||
-          after_sweep(p, depth, p->pad(cur), prm, false, stream) != cudaSuccess)
-        s = fail(SPST_ERR_CUDA, "autotune sweep launch");
-      cur = 1 - cur;
-    }
-    if (s != SPST_OK) break;
-    if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-      s = fail(SPST_ERR_CUDA, "autotune timing");
-      break;
-    }
-    const double per_step = (double)ms / (2.0 * depth);
-    if (per_step < best_ms) {
-      best_ms = per_step;
-      best = depth;
+  for (size_t li = 0; li < layouts.size() && s == SPST_OK; li++) {
+    if (!apply_layout(p, layouts[li]).empty()) continue;
+    for (size_t di = 0; di < depths.size() && s == SPST_OK; di++) {
+      const int depth = depths[di];
+      std::string err;
+      const SweepTables* T = tables_for(p, depth, &err);
+      if (!T) continue;
+      DeviceTables* dt = nullptr;
+      if ((s = ensure_device_tables(p, depth, *T, &dt, stream)) != SPST_OK) break;
+      int cur = 0;
+      float ms = 0.f;
+      for (int k = 0; k < 3 && s == SPST_OK; k++) {
+        if (k == 1 && cudaEventRecord(e0, stream) != cudaSuccess) s = fail(SPST_ERR_CUDA, "cudaEventRecord");
+        spst::Sweep2DParams prm = sweep_params(p, *T, *dt, status);
+        set_output(p, &prm, p->pad(1 - cur), nullptr, false);
+        if (spst::launch_sweep2d(p->tmap[cur], prm, p->num_sms, stream) != cudaSuccess ||
+            after_sweep(p, depth, p->pad(cur), prm, false, stream) != cudaSuccess)
+          s = fail(SPST_ERR_CUDA, "autotune sweep launch");
+        cur = 1 - cur;
+      }
+      if (s != SPST_OK) break;
+      if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        s = fail(SPST_ERR_CUDA, "autotune timing");
+        break;
+      }
+      const double per_step = (double)ms / (2.0 * depth);
+      if (per_step < best_ms) {
+        best_ms = per_step;
+        best_t = depth;
+        best_l = layouts[li];
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != SPST_OK) return s;
-  if (best != p->t) {
-    std::string err;
-    const SweepTables* T = tables_for(p, best, &err);
+  std::string err = apply_layout(p, best_l);
+  if (!err.empty()) return fail(SPST_ERR_UNSUPPORTED, err);
+  if (best_t != p->t) {
+    const SweepTables* T = tables_for(p, best_t, &err);
     if (!T) return fail(SPST_ERR_UNSUPPORTED, err);
     SweepTables chosen = *T;
     p->rem[p->t] = std::move(p->full);
     p->full = std::move(chosen);
-    p->rem.erase(best);
-    // device tables are keyed by depth and stay valid
-    p->t = best;
+    p->rem.erase(best_t);
+    // device tables are keyed by depth and layout and stay valid
+    p->t = best_t;
   }
   p->autotune_pending = false;
   return SPST_OK;
@@ -801,6 +880,127 @@ sparstencil_status run_plan_with_buffers(sparstencil_plan_t p, const float* in, 
 
 }  // namespace spst
 
+namespace {
+
+// Instantiated batch graphs, keyed by everything a captured batch depends on: per job the
+// plan's uid, its workspace, fusion depth and MMA options, the grids and the step count.  A
+// repeated sparstencil_run_batch with the same key replays the graph without preparing,
+// capturing or instantiating again.  Entries holding a plan are dropped when the plan is
+// destroyed; at most kBatchCacheMax are kept (least recently used first out).
+constexpr size_t kBatchCacheMax = 16;
+struct BatchGraph {
+  std::vector<uint64_t> key;
+  int device;
+  cudaGraphExec_t exec;
+};
+std::mutex g_batch_mu;
+std::list<BatchGraph> g_batch_cache;  // most recently used first
+
+std::vector<uint64_t> batch_key(const sparstencil_plan_t* plans, const float* const* in, float* const* out,
+                                const int64_t* steps, int n) {
+  std::vector<uint64_t> k;
+  k.reserve((size_t)n * 7);
+  for (int i = 0; i < n; i++) {
+    const sparstencil_plan_s* p = plans[i];
+    k.push_back(p->uid);
+    k.push_back((uint64_t)(uintptr_t)p->ws);
+    k.push_back(((uint64_t)p->t << 2) | (p->lo_acc ? 1u : 0u) | (p->dense ? 2u : 0u));
+    k.push_back((uint64_t)(uintptr_t)in[i]);
+    k.push_back((uint64_t)(uintptr_t)out[i]);
+    k.push_back((uint64_t)steps[i]);
+    k.push_back(p->autotune_pending || !p->ws_ready ? 1u : 0u);
+  }
+  return k;
+}
+
+// Enqueues a prepared batch on `stream` (captured by the caller): every job's copy-in, then
+// for each sweep index s one launch of the multi-grid sweep kernel per kernel template
+// (FP16 or BF16, single or split words, dimensionality) and per kMultiMaxJobs jobs, over the
+// jobs that have a sweep s, each followed by those jobs' Dirichlet bands or periodic ghost
+// refreshes.  Job j's sweeps alternate between its own two padded grids and its last sweep
+// writes out[j], as in sparstencil_run.
+sparstencil_status enqueue_batch(const sparstencil_plan_t* plans, const float* const* in, float* const* out,
+                                 const int64_t* steps, int n, cudaStream_t stream) {
+  int* status = spst::device_status_word();
+  if (!status) return fail(SPST_ERR_CUDA, "device status word unavailable");
+  std::vector<std::vector<int>> sweeps(n);
+  size_t max_sweeps = 0;
+  for (int i = 0; i < n; i++) {
+    sparstencil_plan_t p = plans[i];
+    if (steps[i] == 0) {
+      SPST_CUDA(cudaMemcpyAsync(out[i], in[i], p->cells() * 4, cudaMemcpyDeviceToDevice, stream), "copy in->out");
+      continue;
+    }
+    sweeps[i].assign((size_t)(steps[i] / p->t), p->t);
+    if (steps[i] % p->t) sweeps[i].push_back((int)(steps[i] % p->t));
+    max_sweeps = std::max(max_sweeps, sweeps[i].size());
+    SPST_CUDA(copy_in(p, in[i], p->pad(0), steps[i], stream, p->maxabs), "pad copy");
+  }
+  // kernel template of a job: FP16 or BF16, single or split words, dimensionality
+  auto group = [&](int i) {
+    return (word_of(plans[i]->dtype) == spst::Word::FP16 ? 1 : 0) + (is_split(plans[i]->dtype) ? 2 : 0) +
+           4 * plans[i]->geo.ndim;
+  };
+  std::vector<CUtensorMap> maps;
+  std::vector<spst::Sweep2DParams> prms;
+  std::vector<int> members;
+  for (size_t s = 0; s < max_sweeps; s++) {
+    std::vector<char> done(n, 0);
+    for (int i0 = 0; i0 < n; i0++) {
+      if (done[i0] || s >= sweeps[i0].size()) continue;
+      const int g = group(i0);
+      members.clear();
+      for (int i = i0; i < n && (int)members.size() < spst::kMultiMaxJobs; i++)
+        if (!done[i] && s < sweeps[i].size() && group(i) == g) {
+          members.push_back(i);
+          done[i] = 1;
+        }
+      maps.clear();
+      prms.clear();
+      for (int i : members) {
+        sparstencil_plan_t p = plans[i];
+        const int depth = sweeps[i][s];
+        std::string err;
+        const SweepTables* T = tables_for(p, depth, &err);
+        if (!T) return fail(SPST_ERR_UNSUPPORTED, err);
+        DeviceTables* dt = nullptr;
+        sparstencil_status st = ensure_device_tables(p, depth, *T, &dt, stream);
+        if (st != SPST_OK) return st;
+        const int cur = (int)(s & 1);
+        spst::Sweep2DParams prm = sweep_params(p, *T, *dt, status);
+        set_output(p, &prm, p->pad(1 - cur), out[i], s + 1 == sweeps[i].size());
+        maps.push_back(p->tmap[cur]);
+        prms.push_back(prm);
+      }
+      SPST_CUDA(spst::launch_sweep2d_multi(maps.data(), prms.data(), (int)members.size(), plans[i0]->num_sms, stream),
+                "batch sweep launch");
+      for (size_t k = 0; k < members.size(); k++) {
+        const int i = members[k];
+        const int cur = (int)(s & 1);
+        SPST_CUDA(after_sweep(plans[i], sweeps[i][s], plans[i]->pad(cur), prms[k], s + 1 == sweeps[i].size(), stream),
+                  "band or ghost launch");
+      }
+    }
+  }
+  return SPST_OK;
+}
+
+void drop_batch_graphs_of(uint64_t uid) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (auto it = g_batch_cache.begin(); it != g_batch_cache.end();) {
+    bool uses = false;
+    for (size_t j = 0; j < it->key.size(); j += 7) uses |= it->key[j] == uid;
+    if (uses) {
+      cudaGraphExecDestroy(it->exec);
+      it = g_batch_cache.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sparstencil_last_error(void) { return g_last_error.c_str(); }
@@ -890,7 +1090,7 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
     else
       p->lo_acc = false;
   }
-  p->autotune_pending = fusion_depth == 0 && p->t_max > 1;
+  p->autotune_pending = fusion_depth == 0;
   p->planner_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out_plan = p.release();
   return SPST_OK;
@@ -911,6 +1111,19 @@ sparstencil_status sparstencil_plan_set_low_accumulator(sparstencil_plan_t plan,
   }
   plan->full = std::move(T);
   plan->rem.clear();
+  return SPST_OK;
+}
+
+sparstencil_status sparstencil_plan_set_layout(sparstencil_plan_t plan, int r1, int pairing) {
+  if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
+  if (!plan->dev_tables.empty()) return fail(SPST_ERR_INVALID, "set the layout before the plan's first run");
+  if (pairing < -1 || pairing > 1) return fail(SPST_ERR_INVALID, "pairing must be -1, 0 or 1");
+  if (plan->geo.ndim == 2 ? (r1 != 16 && r1 != 8) : r1 != plan->geo.r1)
+    return fail(SPST_ERR_UNSUPPORTED, plan->geo.ndim == 2 ? "2D patches are 16 x 8 (r1 = 16) or 8 x 16 (r1 = 8)"
+                                                          : "1D and 3D plans have one patch shape");
+  const std::string err = apply_layout(plan, Layout{r1, (spst::Pairing)pairing});
+  if (!err.empty()) return fail(SPST_ERR_UNSUPPORTED, err);
+  plan->layout_fixed = true;  // a fusion-depth search keeps this layout
   return SPST_OK;
 }
 
@@ -951,6 +1164,7 @@ sparstencil_status sparstencil_plan_set_dense_ablation(sparstencil_plan_t plan, 
 
 sparstencil_status sparstencil_plan_destroy(sparstencil_plan_t plan) {
   if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
+  drop_batch_graphs_of(plan->uid);
   delete plan;
   return SPST_OK;
 }
@@ -964,6 +1178,7 @@ sparstencil_status sparstencil_bind_workspace(sparstencil_plan_t plan, void* dev
   if (!plan || !dev) return fail(SPST_ERR_INVALID, "plan or workspace is null");
   if (((uintptr_t)dev) & 255) return fail(SPST_ERR_INVALID, "workspace must be 256-byte aligned");
   if (bytes < sparstencil_workspace_bytes(plan)) return fail(SPST_ERR_NOMEM, "workspace too small");
+  drop_batch_graphs_of(plan->uid);
   if (plan->ws_owned) cudaFree(plan->ws);
   plan->ws = dev;
   plan->ws_bytes = bytes;
@@ -1050,6 +1265,19 @@ sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const 
     for (int j = 0; j < i; j++)
       if (plans[j] == plans[i]) return fail(SPST_ERR_INVALID, "plans in a batch must be distinct");
   }
+  int dev = 0;
+  SPST_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  {
+    // a batch already captured with the same plans, plan state, grids and steps: replay it
+    const std::vector<uint64_t> key = batch_key(plans, in, out, steps, n);
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (auto it = g_batch_cache.begin(); it != g_batch_cache.end(); ++it) {
+      if (it->device != dev || it->key != key) continue;
+      g_batch_cache.splice(g_batch_cache.begin(), g_batch_cache, it);
+      SPST_CUDA(cudaGraphLaunch(g_batch_cache.front().exec, stream), "launch batch graph");
+      return SPST_OK;
+    }
+  }
   // Everything that allocates, uploads or synchronises happens before the capture: device
   // state, the fusion-depth search of autotuned plans, and the tables of every sweep depth.
   for (int i = 0; i < n; i++) {
@@ -1068,22 +1296,18 @@ sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const 
     }
   }
   SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
-  // One CUDA graph: job i runs on branch i mod nb, the branches run side by side.
-  const int nb = n < 16 ? n : 16;
-  std::vector<cudaStream_t> br(nb, nullptr);
-  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+  // One CUDA graph, captured on a stream of its own: the copy-ins, then one multi-grid sweep
+  // launch per sweep index (consecutive sweeps keep their programmatic dependent launches,
+  // recorded as programmatic edges).
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   sparstencil_status s = SPST_OK;
+  const bool pdl_before = t_pdl_on;
   auto cleanup = [&]() {
-    set_programmatic_launch(true);
+    set_programmatic_launch(pdl_before);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    for (auto e : ev)
-      if (e) cudaEventDestroy(e);
-    for (auto b : br)
-      if (b) cudaStreamDestroy(b);
     if (cap) cudaStreamDestroy(cap);
   };
   auto cuda_ok = [&](cudaError_t e, const char* what) {
@@ -1094,28 +1318,25 @@ sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const 
     cleanup();
     return s;
   }
-  for (int b = 0; b < nb && s == SPST_OK; b++) cuda_ok(cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking), "create branch stream");
-  for (int e = 0; e <= nb && s == SPST_OK; e++) cuda_ok(cudaEventCreateWithFlags(&ev[e], cudaEventDisableTiming), "create event");
-  if (s != SPST_OK) {
-    cleanup();
-    return s;
-  }
-  // plain stream order inside the batch graph: with jobs side by side, a sweep launched early
-  // would hold its SM while waiting for its predecessor (measured 2 % slower with it)
-  set_programmatic_launch(false);
+  set_programmatic_launch(true);
   if (cuda_ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture")) {
-    cuda_ok(cudaEventRecord(ev[nb], cap), "fork event");
-    for (int b = 0; b < nb && s == SPST_OK; b++) cuda_ok(cudaStreamWaitEvent(br[b], ev[nb], 0), "fork wait");
-    for (int i = 0; i < n && s == SPST_OK; i++) s = run_sweeps(plans[i], in[i], out[i], steps[i], br[i % nb]);
-    for (int b = 0; b < nb && s == SPST_OK; b++) {
-      cuda_ok(cudaEventRecord(ev[b], br[b]), "join event");
-      cuda_ok(cudaStreamWaitEvent(cap, ev[b], 0), "join wait");
-    }
+    s = enqueue_batch(plans, in, out, steps, n, cap);
     const cudaError_t ee = cudaStreamEndCapture(cap, &graph);  // always ends the capture
     cuda_ok(ee, "end capture");
   }
   if (s == SPST_OK && cuda_ok(cudaGraphInstantiate(&exec, graph, 0), "instantiate batch graph"))
     cuda_ok(cudaGraphLaunch(exec, stream), "launch batch graph");
+  if (s == SPST_OK) {
+    // keep the executable graph for repeated batches (keyed after the preparation above,
+    // which fixed every plan's workspace and fusion depth)
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    g_batch_cache.push_front(BatchGraph{batch_key(plans, in, out, steps, n), dev, exec});
+    exec = nullptr;
+    while (g_batch_cache.size() > kBatchCacheMax) {
+      cudaGraphExecDestroy(g_batch_cache.back().exec);
+      g_batch_cache.pop_back();
+    }
+  }
   cleanup();  // the launched graph keeps its own copy of the work
   return s;
 }

@@ -25,6 +25,7 @@ struct Sweep2DParams {
   int D;                // planes (3D; 1 for 2D)
   int dim3;             // 1: 3D sweep (Tile3D patches and tiles, 3D TMA box)
   int dim1;             // 1: 1D sweep (Tile1D patches and tiles, rows of the 2D view of the line)
+  int tall;             // 2D: 1 = 8 x 16 patches (16 across, 8 down a tile), 0 = 16 x 8 (8 across, 16 down)
   int G;                // ghost width of the input padded grid
   int tiles_x, tiles_y, tiles_z, num_tiles;
   int P, box_h, box_d;  // shared-memory tile pitch (floats), height (rows), depth (planes) = TMA box
@@ -59,6 +60,23 @@ struct Sweep2DParams {
   int* status;          // device status word
   unsigned long long wait_ns;  // bound of every device-side wait
 };
+
+// A batch launch: up to kMultiMaxJobs grids swept by one launch of at most kMultiMaxCtas CTAs
+// (job j gets CTAs cta_first[j] .. cta_first[j] + cta_count[j] - 1).  Passed by value as the
+// kernel's parameter block (about 23 KB).
+constexpr int kMultiMaxJobs = 64, kMultiMaxCtas = 256;
+struct MultiSweepParams {
+  CUtensorMap tmap[kMultiMaxJobs];  // 64-byte aligned: first member
+  Sweep2DParams job[kMultiMaxJobs];
+  int cta_first[kMultiMaxJobs], cta_count[kMultiMaxJobs];
+  int16_t cta_job[kMultiMaxCtas];
+  int njobs, nctas;
+};
+// Launches one batch sweep: job j's sweep with tensor map maps[j] and parameters prm[j] (the
+// jobs share the kernel template: FP16 or BF16, single or split words, dimensionality).  The
+// SMs are shared out by tile count (each job gets at least one CTA).  Returns the launch error.
+cudaError_t launch_sweep2d_multi(const CUtensorMap* maps, const Sweep2DParams* prm, int njobs, int num_sms,
+                                 cudaStream_t stream);
 
 // Shared-memory bytes the sweep kernel needs for this geometry (with p.nslots chunk slots).
 size_t sweep2d_smem_bytes(const Sweep2DParams& p);

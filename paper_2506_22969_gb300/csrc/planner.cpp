@@ -569,7 +569,7 @@ int pack_pairs_min_repeats(const std::vector<std::pair<int, int>>& pairs, const 
 // 2D sweep tables.
 // ---------------------------------------------------------------------------------------
 std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, const PlanGeometry& geo, Word word,
-                                  int max_pieces, bool drop_zero_pairs, SweepTables* out) {
+                                  int max_pieces, bool drop_zero_pairs, SweepTables* out, Pairing pairing) {
   SweepTables& T = *out;
   T = SweepTables();
   const bool d3 = geo.ndim == 3, d1 = geo.ndim == 1;
@@ -578,9 +578,10 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   T.kt = 2 * R + 1;
   const int kt = T.kt;
   // 1D: one staircase block (r2 = r3 = 1), so the 2D formulas below hold with mb = 1
-  const int r1 = d1 ? Tile1D::R1 : (d3 ? Tile3D::R1 : Tile2D::R1);
-  const int r2 = d1 ? 1 : (d3 ? Tile3D::R2 : Tile2D::R2), r3 = d3 ? Tile3D::R3 : 1;
+  const int r1 = d1 ? Tile1D::R1 : (d3 ? Tile3D::R1 : geo.r1);
+  const int r2 = d1 ? 1 : (d3 ? Tile3D::R2 : geo.r2), r3 = d3 ? Tile3D::R3 : 1;
   const int M = d1 ? Tile1D::M : (d3 ? Tile3D::M : Tile2D::M);
+  if (!d1 && !d3 && (r1 * r2 != Tile2D::M || (r1 != 16 && r1 != 8))) return "2D patches are 16 x 8 or 8 x 16";
   T.r1 = r1;
   T.r2 = r2;
   T.r3 = r3;
@@ -638,7 +639,7 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
   std::vector<int> nzcols;
   for (int kap = 0; kap < kp; kap++)
     if (colnz[kap]) nzcols.push_back(kap);
-  if (drop_zero_pairs && (int)nzcols.size() < kp) {
+  if (drop_zero_pairs && (int)nzcols.size() < kp && pairing != Pairing::Algorithm1) {
     const int n = (int)nzcols.size();
     std::vector<std::vector<uint64_t>> rows(n, std::vector<uint64_t>((size_t)(M + 63) / 64, 0));
     for (int i = 0; i < n; i++)
@@ -666,7 +667,8 @@ std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, cons
       }
     }
     const int chunk_pairs = Tile2D::KCHUNK / 2;
-    if ((mpairs.size() + chunk_pairs - 1) / chunk_pairs < (kept.size() + chunk_pairs - 1) / chunk_pairs) {
+    if (pairing == Pairing::Matching ||
+        (mpairs.size() + chunk_pairs - 1) / chunk_pairs < (kept.size() + chunk_pairs - 1) / chunk_pairs) {
       kept = std::move(mpairs);
       T.zero_cols = unmatched;
       T.dropped_pairs = 0;

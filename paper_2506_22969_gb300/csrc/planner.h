@@ -89,7 +89,14 @@ struct PlanGeometry {
   int box_h = 0;                  // TMA box height
   int64_t tiles_x = 0, tiles_y = 0, tiles_z = 1, num_tiles = 0;
   int box_d = 1;                  // TMA box depth (3D)
+  // 2D crush factors (r1 outputs along x by r2 along y per patch, r1 * r2 = 128): (16, 8), the
+  // default, or (8, 16); the tile stays 128 x 128 outputs either way
+  int r1 = Tile2D::R1, r2 = Tile2D::R2;
 };
+
+// Column pairing of the 2:4 conversion: Algorithm 1's pairs, a maximum matching on the
+// stencil's actual support, or whichever of the two needs fewer K chunks.
+enum class Pairing { Auto = -1, Algorithm1 = 0, Matching = 1 };
 
 // Composes t steps of the offset-indexed cube w (radius r, ndim axes) into one cube of
 // radius t*r (FP64): W_{j+1}[o] = sum_{a+b=o} W_j[a] w[b].
@@ -118,12 +125,13 @@ int pack_pairs_min_repeats(const std::vector<std::pair<int, int>>& pairs, const 
 // block.  For two levels it is hierarchical_matching.
 std::vector<std::pair<int, int>> hierarchical_matching_nd(const std::vector<int>& sizes, int k);
 
-// Builds the sweep tables of a 2D (geo.ndim = 2, Tile2D) or 3D (geo.ndim = 3, Tile3D) stencil
+// Builds the sweep tables of a 2D (geo.ndim = 2, patches of geo.r1 x geo.r2) or 3D (geo.ndim = 3, Tile3D) stencil
 // (fused cube `wfused` of radius R) for the ghost width G, tile pitch P (and box height of a
 // 3D tile plane) of `geo`, and operand encoding `word`.  max_pieces: number of 16-bit pieces
 // the weights may use (1..3).  Returns an empty string or an error message.
 std::string build_sweep_tables_2d(const std::vector<double>& wfused, int R, const PlanGeometry& geo, Word word,
-                                  int max_pieces, bool drop_zero_pairs, SweepTables* out);
+                                  int max_pieces, bool drop_zero_pairs, SweepTables* out,
+                                  Pairing pairing = Pairing::Auto);
 
 // Analytical cost model of Sec. 3.3 (T = max(T_compute, T_memory)) for a candidate (r1, r2):
 // returns seconds per sweep for an H x W grid.  Used to rank layouts.

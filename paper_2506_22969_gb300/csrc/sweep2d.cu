@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <type_traits>
 
 #include "kernels.h"
@@ -270,7 +271,7 @@ __device__ __forceinline__ void trace(bool on, int role, int li, int ev) {
 #endif
 }
 // Chunk-level clock64 stamps in CTA 0 for tile 1: [source][chunk < 16][4], sources 0 and 1
-// the first and the last gather warp (chunk start, halo loads issued + LUT, slot free, chunk
+// the first and the last gather warp (chunk start, slot free, stores issued, chunk
 // published), source 2 the MMA issuer (chunk's B'' complete, MMAs issued, -, -).
 constexpr int kTraceChunkWords = 3 * 16 * 4 + 2 * 16 * 16;  // + [gather warp][chunk] publish / stored stamps
 __device__ unsigned long long g_trace_chunks[kTraceChunkWords];
@@ -315,9 +316,11 @@ constexpr int kItems = 64 / kGatherWarps;                        // patch pairs 
 // 8 x 4 x 4 patches, 64 x 16 x 16 tiles).  Patch n of a 3D tile, with n = a*16 + h*8 + b, is
 // (px, py, pz) = (4(a&1) + 2h + (b&1), b>>1, a>>1): the two half-warps of a gather warp take
 // patches n and n+8, 16 words apart in x, as in 2D.
+// The sweep of one grid by CTA `cta` of the `ncta` CTAs given to it: tiles cta, cta + ncta, ...
+// tmap_in: the TMA map of the input padded grid (kernel parameter space).
 template <int FP16, int SPLIT, int DIM>
-__global__ void __launch_bounds__(kSweepThreads, 1)
-    sweep2d_kernel(const __grid_constant__ CUtensorMap tmap_in, const Sweep2DParams p) {
+__device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Sweep2DParams& p, const int cta,
+                                           const int ncta) {
   constexpr bool DIM3 = DIM == 3, DIM1 = DIM == 1;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     }
   }
 
-  const int ntiles_cta = (p.num_tiles > (int)blockIdx.x) ? (p.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int ntiles_cta = (p.num_tiles > cta) ? (p.num_tiles - 1 - cta) / ncta + 1 : 0;
   const bool tr = (blockIdx.x == 0) && g_trace_on;
 
   if (warp == 0) {
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       for (int li = 0; li < ntiles_cta; li++) {
         const int stage = li & 1;
         if (li >= 2 && !mbar_wait(bar(BAR_HEMPTY + stage), ((li >> 1) - 1) & 1, wait_ns, abort_flag, p.status)) break;
-        const int tt = (int)blockIdx.x + li * (int)gridDim.x;
+        const int tt = cta + li * ncta;
         const uint32_t dst = sbase + (uint32_t)stage * L.halo_stride;
         trace(tr, 0, li, 0);
         mbar_expect_tx(bar(BAR_HFULL + stage), bytes);
@@ -468,21 +471,21 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           asm volatile(
               "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
                   dst),
-              "l"(&tmap_in), "r"(0), "r"(tt * (k1dTile / k1dRow)), "r"(bar(BAR_HFULL + stage))
+              "l"(tmap_in), "r"(0), "r"(tt * (k1dTile / k1dRow)), "r"(bar(BAR_HFULL + stage))
               : "memory");
         } else if (DIM3) {
           const int tx = tt % p.tiles_x, ty = (tt / p.tiles_x) % p.tiles_y, tz = tt / (p.tiles_x * p.tiles_y);
           asm volatile(
               "cp.async.bulk.tensor.3d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
                   dst),
-              "l"(&tmap_in), "r"(tx * 64), "r"(ty * 16), "r"(tz * 16), "r"(bar(BAR_HFULL + stage))
+              "l"(tmap_in), "r"(tx * 64), "r"(ty * 16), "r"(tz * 16), "r"(bar(BAR_HFULL + stage))
               : "memory");
         } else {
           const int x0 = (tt % p.tiles_x) * 128, y0 = (tt / p.tiles_x) * 128;
           asm volatile(
               "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
                   dst),
-              "l"(&tmap_in), "r"(x0), "r"(y0), "r"(bar(BAR_HFULL + stage))
+              "l"(tmap_in), "r"(x0), "r"(y0), "r"(bar(BAR_HFULL + stage))
               : "memory");
         }
         issued++;
@@ -596,7 +599,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     // row rho of a patch: 2D (ry, rx) = (rho / 16, rho % 16); 3D (rz, ry, rx) = (rho / 32,
     // rho / 8 % 4, rho % 8)
     const int rz = DIM3 ? rho >> 5 : 0;
-    const int ry = DIM3 ? (rho >> 3) & 3 : rho >> 4, rx = DIM3 ? rho & 7 : rho & 15;
+    const int ry = DIM3 ? (rho >> 3) & 3 : (p.tall ? rho >> 3 : rho >> 4);
+    const int rx = DIM3 ? rho & 7 : (p.tall ? rho & 7 : rho & 15);
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
     const uint32_t cv_s = sbase + L.off_cv;
     const float out_scale = p.wscale * dscale_inv;  // undoes the weight and data scales (powers of two)
@@ -608,7 +612,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       if (!warp_wait(bar(BAR_CVFULL + (li & 1)), (li >> 1) & 1, wait_ns, abort_flag, p.status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       trace(tr && warp == 4 && lane == 0, 3, li, 0);
-      const int tt = (int)blockIdx.x + li * (int)gridDim.x;
+      const int tt = cta + li * ncta;
       if (DIM1) {
         // column n of the accumulator is patch n: outputs x0 + 128n + rho, a lane per output
         const int64_t x0 = (int64_t)tt * k1dTile;
@@ -718,21 +722,29 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           }
           continue;
         }
-        // columns cg*16 .. +15 are patches (py, px) = (cg/4*8 + j%8, (2cg + j/8) % 8)
-        const int py0 = (cg >> 2) << 3, px0 = (2 * cg) & 7;
-        if (full) {
+        // column cg*16 + j is the patch whose outputs start yoff rows and xoff columns into
+        // the tile: 16 x 8 patches (py, px) = (cg/4*8 + j%8, (2cg + j/8) % 8); tall 8 x 16
+        // patches (py, px) = (cg, 4((j%8)/2) + 2(j/8) + j%2)
+        auto yoff = [&](int j) { return p.tall ? cg * 16 : (((cg >> 2) << 3) + (j & 7)) * 8; };
+        auto xoff = [&](int j) { return p.tall ? (4 * ((j & 7) >> 1) + 2 * (j >> 3) + (j & 1)) * 8 : (((2 * cg) & 7) + (j >> 3)) * 16; };
+        if (full && !p.tall) {
+          const int py0 = (cg >> 2) << 3, px0 = (2 * cg) & 7;
 #pragma unroll
           for (int j = 0; j < 16; j++) obase[(int64_t)(py0 + (j & 7)) * pitch8 + (px0 + (j >> 3)) * 16] = val[j];
+        } else if (full) {
+          const int64_t row = (int64_t)cg * 2 * pitch8;  // 16 rows per patch
+#pragma unroll
+          for (int j = 0; j < 16; j++) obase[row + (4 * ((j & 7) >> 1) + 2 * (j >> 3) + (j & 1)) * 8] = val[j];
         } else {
 #pragma unroll
           for (int j = 0; j < 16; j++) {
-            const int y = y0 + (py0 + (j & 7)) * 8 + ry, x = x0 + (px0 + (j >> 3)) * 16 + rx;
-            if (y < p.H && x < p.W) obase[(int64_t)(py0 + (j & 7)) * pitch8 + (px0 + (j >> 3)) * 16] = val[j];
+            const int y = y0 + yoff(j) + ry, x = x0 + xoff(j) + rx;
+            if (y < p.H && x < p.W) obase[(int64_t)yoff(j) * p.out_pitch + xoff(j)] = val[j];
           }
         }
         if (ghost) {
           for (int j = 0; j < 16; j++) {
-            const int y = y0 + (py0 + (j & 7)) * 8 + ry, x = x0 + (px0 + (j >> 3)) * 16 + rx;
+            const int y = y0 + yoff(j) + ry, x = x0 + xoff(j) + rx;
             if (y >= p.H || x >= p.W) continue;
             const bool by = (y < G) || (y >= p.H - G), bx = (x < G) || (x >= p.W - G);
             if (!by && !bx) continue;
@@ -777,6 +789,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         const int a = n >> 4, b = n & 7;
         const int px = ((a & 1) << 2) | (h << 1) | (b & 1), py = b >> 1, pz = a >> 1;
         base_i[i] = 4 * (pz * 4 * p.box_h * P + py * 4 * P + px * 8);
+      } else if (p.tall) {
+        // 8 x 16 patches: column n = 16 py + 8 hb + e is patch (px, py) = (4(e>>1) + 2hb + (e&1),
+        // n >> 4), so the half-warps' patches (hb = h) are two patches, 16 words, apart in x
+        const int e = n & 7, hb = (n >> 3) & 1;
+        const int px = 4 * (e >> 1) + 2 * hb + (e & 1), py = n >> 4;
+        base_i[i] = 4 * (py * 16 * P + px * 8);
       } else {
         const int px = (n >> 3) & 7, py = ((n >> 6) << 3) + (n & 7);
         base_i[i] = 4 * (py * 8 * P + px * 16);
@@ -801,7 +819,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       for (int i = 0; i < kItems; i++) {
         ba[i] = tile_s + (uint32_t)base_i[i];
         // the patch constant: the mean of the 8 inputs in the middle of the patch's outputs
-        // (2D rows 3-4 x columns 6-9 of its 8 x 16, 3D the central 2 x 2 x 2 of its 4 x 4 x 8).
+        // (2D rows 3-4 x columns 6-9 of its 8 rows x 16 columns, rows 7-8 x columns 2-5 of a
+        // tall 16 x 8 patch; 3D the central 2 x 2 x 2 of its 4 x 4 x 8).
         // Any c gives the same sum (sum w (u - c) + c sum w); the MMAs round their FP32
         // partial sums, so c should keep |u - c| small: near the local value for smooth data
         // with an offset, near the local mean (not one sample of it) for rough zero-mean data
@@ -810,7 +829,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         // the same two partial sums, and FP32 addition is commutative).
         const uint32_t m0 = ba[i] + 4u * (uint32_t)(DIM1 ? G + 60
                                                          : DIM3 ? (G + 1) * p.box_h * P + (G + 1) * P + G + 3
-                                                                : (G + 3) * P + G + 6);
+                                                                : p.tall ? (G + 7) * P + G + 2 : (G + 3) * P + G + 6);
         float cs = lds_f32(m0 + c_off);
         cs += __shfl_xor_sync(0xffffffffu, cs, 1);
         cs += __shfl_xor_sync(0xffffffffu, cs, 2);
@@ -828,13 +847,18 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(BAR_CVFULL + cvs));
       bool ok = true;
+      // Software pipeline: chunk kc's values are loaded one chunk ahead, and the lookup-table
+      // entries of chunk kc+2 two chunks ahead, so no shared-memory load of this warp waits
+      // on another one; the next chunk's loads are issued after this chunk's proxy fence,
+      // which then waits for this chunk's stores only.
       const bool trc = tr && (gw == 0 || gw == kGatherWarps - 1) && lane == 0 && li == 1;
       const int tsrc = gw == 0 ? 0 : 1;
-      // software pipeline: chunk kc+1's loads are issued before chunk kc's values are used
       float va[kItems], vb[kItems];
+      int2 lab_next;  // LUT entries of the next chunk to load
       {
-        const int2 lab = lds_v2_s32(lut_sa);
-        const uint32_t la = 4u * (uint32_t)lab.x, lb = 4u * (uint32_t)lab.y;
+        const int2 lab0 = lds_v2_s32(lut_sa);
+        lab_next = p.kchunks > 1 ? lds_v2_s32(lut_sa + 128u) : lab0;
+        const uint32_t la = 4u * (uint32_t)lab0.x, lb = 4u * (uint32_t)lab0.y;
 #pragma unroll
         for (int i = 0; i < kItems; i++) {
           va[i] = lds_f32(ba[i] + la);
@@ -843,23 +867,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       }
       for (int kc = 0; kc < p.kchunks; kc++) {
         trace_chunk(trc, tsrc, kc, 0);
-        float na[kItems], nb[kItems];
-        if (kc + 1 < p.kchunks) {
-          const int2 lab = lds_v2_s32(lut_sa + 128u * (uint32_t)(kc + 1));
-          const uint32_t la = 4u * (uint32_t)lab.x, lb = 4u * (uint32_t)lab.y;
-#pragma unroll
-          for (int i = 0; i < kItems; i++) {
-            na[i] = lds_f32(ba[i] + la);
-            nb[i] = lds_f32(ba[i] + lb);
-          }
-        }
-        trace_chunk(trc, tsrc, kc, 1);
         if (used >= (uint32_t)p.nslots &&
             !warp_wait(bar(BAR_BEMPTY + slot), sphase ^ 1u, wait_ns, abort_flag, p.status)) {
           ok = false;
           break;
         }
-        trace_chunk(trc, tsrc, kc, 2);
+        trace_chunk(trc, tsrc, kc, 1);
         const uint32_t bs = sbase + L.off_b + slot * L.slot_bytes;
 #pragma unroll
         for (int i = 0; i < kItems; i++) {
@@ -873,6 +886,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
             sts_u32(bs + kPieceBytes + soff_i[i], pack2(da - ha, db - hb, FP16));
           }
         }
+        trace_chunk(trc, tsrc, kc, 2);
 #if SPST_TRACE
         if (tr && li == 1 && lane == 0 && kc < 16) {
           unsigned long long c;
@@ -883,11 +897,6 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(BAR_BFULL + slot));
-#pragma unroll
-        for (int i = 0; i < kItems; i++) {
-          va[i] = na[i];
-          vb[i] = nb[i];
-        }
         used++;
         if (++slot == (uint32_t)p.nslots) {
           slot = 0;
@@ -901,6 +910,15 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           g_trace_chunks[3 * 16 * 4 + gw * 16 + kc] = c;
         }
 #endif
+        if (kc + 1 < p.kchunks) {
+          const uint32_t la = 4u * (uint32_t)lab_next.x, lb = 4u * (uint32_t)lab_next.y;
+#pragma unroll
+          for (int i = 0; i < kItems; i++) {
+            va[i] = lds_f32(ba[i] + la);
+            vb[i] = lds_f32(ba[i] + lb);
+          }
+          if (kc + 2 < p.kchunks) lab_next = lds_v2_s32(lut_sa + 128u * (uint32_t)(kc + 2));
+        }
       }
       if (!ok) break;
       __syncwarp();
@@ -914,6 +932,23 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// One grid per launch: every CTA takes its share of the grid's tiles.
+template <int FP16, int SPLIT, int DIM>
+__global__ void __launch_bounds__(kSweepThreads, 1)
+    sweep2d_kernel(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant__ Sweep2DParams p) {
+  sweep_body<FP16, SPLIT, DIM>(&tmap_in, p, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Many grids per launch (a batch's sweeps of one index): CTA b works on job cta_job[b], as CTA
+// b - cta_first[job] of the cta_count[job] CTAs given to that job, with the job's own tables,
+// tensor map and output; a CTA never changes job, so its set-up (TMEM tables, lookup table)
+// is the single-grid one.
+template <int FP16, int SPLIT, int DIM>
+__global__ void __launch_bounds__(kSweepThreads, 1) sweep2d_multi_kernel(const __grid_constant__ MultiSweepParams m) {
+  const int j = m.cta_job[blockIdx.x];
+  sweep_body<FP16, SPLIT, DIM>(&m.tmap[j], m.job[j], (int)blockIdx.x - m.cta_first[j], m.cta_count[j]);
 }
 
 }  // namespace
@@ -968,6 +1003,93 @@ namespace {
 thread_local bool t_pdl = true;
 }
 void sweep2d_set_programmatic_launch(bool on) { t_pdl = on; }
+
+namespace {
+// The chunk-slot count and early-TMA flag of a sweep (as launch_sweep2d sets them); false if
+// the geometry does not fit.
+bool finish_params(Sweep2DParams* p) {
+  p->nslots = sweep2d_max_slots(*p);
+  if (p->nslots < 2) return false;
+  const SmemLayout L(*p);
+  const size_t need = staging_bytes(*p);
+  p->early_tma = (need <= (size_t)(L.off_lut - L.halo_stride)) ? 1 : 0;
+  return need <= (size_t)L.off_lut;
+}
+
+template <typename K>
+K pick_kernel(const Sweep2DParams& p, K k100, K k110, K k103, K k113, K k101, K k111, K k000, K k010, K k003,
+              K k013, K k001, K k011) {
+  // naming: k<fp16><split><dim>, dim 0 = 2D
+  if (p.dim3) return p.fp16 ? (p.b_pieces > 1 ? k113 : k103) : (p.b_pieces > 1 ? k013 : k003);
+  if (p.dim1) return p.fp16 ? (p.b_pieces > 1 ? k111 : k101) : (p.b_pieces > 1 ? k011 : k001);
+  return p.fp16 ? (p.b_pieces > 1 ? k110 : k100) : (p.b_pieces > 1 ? k010 : k000);
+}
+}  // namespace
+
+cudaError_t launch_sweep2d_multi(const CUtensorMap* maps, const Sweep2DParams* prm, int njobs, int num_sms,
+                                 cudaStream_t stream) {
+  if (njobs < 1 || njobs > kMultiMaxJobs) return cudaErrorInvalidValue;
+  thread_local MultiSweepParams m;  // about 23 KB: kept off the stack
+  std::memset(&m, 0, sizeof(m));
+  m.njobs = njobs;
+  size_t smem = 0;
+  int64_t total_tiles = 0;
+  for (int j = 0; j < njobs; j++) {
+    m.tmap[j] = maps[j];
+    m.job[j] = prm[j];
+    if (!finish_params(&m.job[j])) return cudaErrorInvalidConfiguration;
+    if (m.job[j].fp16 != prm[0].fp16 || m.job[j].b_pieces != prm[0].b_pieces || m.job[j].dim3 != prm[0].dim3 ||
+        m.job[j].dim1 != prm[0].dim1)
+      return cudaErrorInvalidValue;
+    const size_t s = sweep2d_smem_bytes(m.job[j]);
+    smem = s > smem ? s : smem;
+    total_tiles += m.job[j].num_tiles;
+  }
+  // CTAs: one per job, then the rest one at a time to the job with the most tiles per CTA
+  int ctas = num_sms < kMultiMaxCtas ? num_sms : kMultiMaxCtas;
+  if (total_tiles < ctas) ctas = (int)total_tiles;
+  if (ctas < njobs) return cudaErrorInvalidConfiguration;
+  for (int j = 0; j < njobs; j++) m.cta_count[j] = 1;
+  for (int c = njobs; c < ctas; c++) {
+    int best = -1;
+    double best_load = 0.0;
+    for (int j = 0; j < njobs; j++) {
+      if (m.cta_count[j] >= m.job[j].num_tiles) continue;
+      const double load = (double)m.job[j].num_tiles / m.cta_count[j];
+      if (load > best_load) {
+        best_load = load;
+        best = j;
+      }
+    }
+    if (best < 0) break;
+    m.cta_count[best]++;
+  }
+  int next = 0;
+  for (int j = 0; j < njobs; j++) {
+    m.cta_first[j] = next;
+    for (int c = 0; c < m.cta_count[j]; c++) m.cta_job[next + c] = (int16_t)j;
+    next += m.cta_count[j];
+  }
+  m.nctas = next;
+  auto kern = pick_kernel(m.job[0], sweep2d_multi_kernel<1, 0, 2>, sweep2d_multi_kernel<1, 1, 2>,
+                          sweep2d_multi_kernel<1, 0, 3>, sweep2d_multi_kernel<1, 1, 3>, sweep2d_multi_kernel<1, 0, 1>,
+                          sweep2d_multi_kernel<1, 1, 1>, sweep2d_multi_kernel<0, 0, 2>, sweep2d_multi_kernel<0, 1, 2>,
+                          sweep2d_multi_kernel<0, 0, 3>, sweep2d_multi_kernel<0, 1, 3>, sweep2d_multi_kernel<0, 0, 1>,
+                          sweep2d_multi_kernel<0, 1, 1>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)m.nctas);
+  cfg.blockDim = dim3(kSweepThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = t_pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, m);
+}
 
 cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p_in, int num_sms, cudaStream_t stream) {
   Sweep2DParams p = p_in;

@@ -100,6 +100,52 @@ def test_sparse_matches_oracle(torch_cuda, oracle_mod, shape, r, recipe, dims, s
         _assert_tol(*_rel(got[band], ref[band]), dtype, "band")
 
 
+@pytest.mark.parametrize("shape,r,recipe,dims,steps,bc,dtype,t", [
+    ("box", 1, "random", (300, 260), 20, "periodic", "bf16_split", 1),
+    ("box", 1, "random", (300, 260), 13, "periodic", "bf16_split", 6),
+    ("star", 1, "heat", (512, 512), 8, "dirichlet", "fp16", 3),
+    ("box", 3, "gaussian", (260, 300), 8, "periodic", "bf16", 2),
+    ("star", 3, "gaussian", (200, 256), 5, "dirichlet", "fp16_split", 1),
+    ("box", 2, "random", (130, 200), 7, "dirichlet", "bf16_split", 2),
+])
+def test_tall_patch_layout_matches_oracle(torch_cuda, oracle_mod, shape, r, recipe, dims, steps, bc, dtype, t):
+    """8 x 16 patches (sparstencil_plan_set_layout r1 = 8): the gather's patch map, the
+    epilogue's output map, the periodic ghost images and the Dirichlet band all follow it."""
+    torch = torch_cuda
+    w = inputs.stencil_weights(shape, 2, r, recipe, seed=11)
+    u = inputs.uniform01(5, dims)
+    ref = oracle_mod.run(u, w, bc, steps)
+    plan = binding.Plan(w, dims, dtype=dtype, bc=bc, fusion_depth=t, shape=shape, layout=(8, -1))
+    assert plan.info().r1 == 8 and plan.info().r2 == 16
+    x = torch.from_numpy(u).cuda()
+    y = torch.full_like(x, float("nan"))
+    plan.run(x, y, steps)
+    assert binding.device_status() == 0
+    got = y.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got))
+    _assert_tol(*oracle_mod.rel_errors(got, ref), dtype)
+
+
+def test_layout_search_matches_oracle(torch_cuda, oracle_mod):
+    """fusion_depth 0 searches depth x patch shape (x pairing for a star): the chosen layout is
+    reported and the run meets the tolerance; a second run repeats it bit for bit."""
+    torch = torch_cuda
+    for shape, r, recipe in (("box", 1, "random"), ("star", 3, "gaussian")):
+        w = inputs.stencil_weights(shape, 2, r, recipe, seed=4)
+        u = inputs.uniform01(9, (520, 390))
+        plan = binding.Plan(w, u.shape, dtype="bf16_split", bc="periodic", fusion_depth=0, shape=shape)
+        x = torch.from_numpy(u).cuda()
+        y1, y2 = torch.empty_like(x), torch.empty_like(x)
+        plan.run(x, y1, 12)
+        info = plan.info()
+        assert info.r1 in (16, 8) and info.r1 * info.r2 == 128 and info.pairing in (0, 1)
+        plan.run(x, y2, 12)
+        assert binding.device_status() == 0
+        assert torch.equal(y1, y2)
+        ref = oracle_mod.run(u, w, "periodic", 12)
+        _assert_tol(*oracle_mod.rel_errors(y1.cpu().numpy().astype(np.float64), ref), "bf16_split", shape)
+
+
 def test_zero_and_one_step(torch_cuda, oracle_mod):
     w = inputs.stencil_weights("box", 2, 1, "random", seed=3)
     u = inputs.uniform01(6, (200, 136))
@@ -177,6 +223,37 @@ def test_direct_fp32_matches_oracle(torch_cuda, oracle_mod):
         ref = oracle_mod.run(u, w, bc, 9)
         l2, linf = oracle_mod.rel_errors(out.cpu().numpy(), ref)
         assert l2 <= 1e-6 and linf <= 1e-5, (shape, r, bc, l2, linf)
+
+
+@pytest.mark.parametrize("dims,r,bc", [
+    ((20, 64), 4, "periodic"),     # fewer rows than a warp's segment: every row wraps once at most
+    ((70, 132), 3, "dirichlet"),   # width not a multiple of 128: a partly idle warp
+    ((130, 516), 1, "periodic"),   # several warps across, ragged last segment
+    ((96, 260), 2, "dirichlet"),
+])
+def test_direct_fp32_ragged(torch_cuda, oracle_mod, dims, r, bc):
+    """The register-marching FP32 comparator on ragged 2D grids (widths a multiple of 4)."""
+    torch = torch_cuda
+    w = inputs.stencil_weights("box", 2, r, "random", seed=9)
+    u = inputs.uniform01(3, dims)
+    x = torch.from_numpy(u).cuda()
+    out, work = torch.empty_like(x), torch.empty_like(x)
+    binding.direct_run(w, x, out, work, 5, bc=bc)
+    l2, linf = oracle_mod.rel_errors(out.cpu().numpy(), oracle_mod.run(u, w, bc, 5))
+    assert l2 <= 1e-6 and linf <= 1e-5, (l2, linf)
+
+
+@pytest.mark.parametrize("dims,bc", [((5, 12, 132), "periodic"), ((37, 9, 260), "dirichlet"), ((33, 20, 36), "periodic")])
+def test_direct_fp32_3d_ragged(torch_cuda, oracle_mod, dims, bc):
+    """The 3D radius-1 comparator with fewer planes than a warp's segment and ragged widths."""
+    torch = torch_cuda
+    w = inputs.stencil_weights("box", 3, 1, "random", seed=10)
+    u = inputs.uniform_pm1(4, dims)
+    x = torch.from_numpy(u).cuda()
+    out, work = torch.empty_like(x), torch.empty_like(x)
+    binding.direct_run(w, x, out, work, 4, bc=bc)
+    l2, linf = oracle_mod.rel_errors(out.cpu().numpy(), oracle_mod.run(u, w, bc, 4))
+    assert l2 <= 1e-6 and linf <= 1e-5, (l2, linf)
 
 
 def test_direct_fp32_3d(torch_cuda, oracle_mod):
@@ -301,6 +378,18 @@ def test_batch_graph_equals_individual_runs(torch_cuda):
     assert binding.device_status() == 0
     for a, b in zip(alone, outs):
         assert torch.equal(a, b)
+    # the same batch again replays the kept graph; new inputs in the same buffers flow through it
+    for o in outs:
+        o.fill_(float("nan"))
+    for k, x in enumerate(xs):
+        x.copy_(torch.from_numpy(inputs.uniform01(60 + k, tuple(x.shape))).cuda())
+    binding.run_batch(plans, xs, outs, steps)
+    torch.cuda.synchronize()
+    assert binding.device_status() == 0
+    for plan, x, o, T in zip(plans, xs, outs, steps):
+        y = torch.empty_like(x)
+        plan.run(x, y, T)
+        assert torch.equal(y, o)
 
 
 CASES_3D = [

@@ -78,18 +78,26 @@ CASES = [("star", 1, "heat", 1, "bf16"), ("box", 1, "random", 1, "bf16_split"), 
          ("box", 6, "gaussian", 1, "bf16_split"), ("star", 9, "gaussian", 1, "fp16")]
 
 
-@pytest.mark.parametrize("shape,r,recipe,t,dtype", CASES)
-def test_planner_tables_against_oracle(lib, oracle_mod, shape, r, recipe, t, dtype):
+# the tall 8 x 16 patch layout (sparstencil_plan_set_layout r1 = 8)
+CASES_TALL = [("star", 1, "heat", 1, "bf16"), ("box", 1, "random", 3, "bf16_split"),
+              ("star", 3, "gaussian", 1, "bf16_split"), ("box", 3, "gaussian", 2, "fp16")]
+
+
+@pytest.mark.parametrize("r1", [16, 8])
+@pytest.mark.parametrize("shape,r,recipe,t,dtype", CASES + CASES_TALL)
+def test_planner_tables_against_oracle(lib, oracle_mod, shape, r, recipe, t, dtype, r1):
+    if r1 == 8 and (shape, r, recipe, t, dtype) not in CASES_TALL:
+        pytest.skip("tall layout checked on its own cases")
     w = inputs.stencil_weights(shape, 2, r, recipe, seed=7)
-    plan = binding.Plan(w, (300, 260), dtype=dtype, bc="periodic", fusion_depth=t, shape=shape)
+    plan = binding.Plan(w, (300, 260), dtype=dtype, bc="periodic", fusion_depth=t, shape=shape, layout=(r1, -1))
     info = plan.info()
     tb = plan.tables()
     k = 2 * t * r + 1
     # composed weights equal the oracle's t-step impulse response
     np.testing.assert_allclose(tb["fused_w"], _composed(w, t), rtol=1e-13, atol=1e-16)
     wf32 = tb["fused_w"].astype(np.float32).astype(np.float64)
-    A, alg1 = _oracle_order(wf32, k, 16, 8)
-    assert info.r1 == 16 and info.r2 == 8 and info.kprime == A.shape[1]
+    A, alg1 = _oracle_order(wf32, k, r1, 128 // r1)
+    assert info.r1 == r1 and info.r2 == 128 // r1 and info.kprime == A.shape[1]
     order = tb["order"]
     assert info.kpad == len(order) and info.kpad % 32 == 0
 
@@ -176,27 +184,35 @@ def _emulate_sweep(plan, tb, u, bc, dense):
             blk = up[ty * 128:ty * 128 + bh, tx * 128:tx * 128 + P]
             tile[:blk.shape[0], :blk.shape[1]] = blk
             flat = tile.ravel()
+            r1 = info.r1
+            r2 = 128 // r1
             for n in range(128):
-                px, py = (n >> 3) & 7, ((n >> 6) << 3) + (n & 7)
-                base = py * 8 * P + px * 16
+                if r1 == 16:
+                    px, py = (n >> 3) & 7, ((n >> 6) << 3) + (n & 7)
+                else:  # tall 8 x 16 patches: n = 16 py + 8 hb + e
+                    e, hb = n & 7, (n >> 3) & 1
+                    px, py = 4 * (e >> 1) + 2 * hb + (e & 1), n >> 4
+                base = py * r2 * P + px * r1
                 col = dense @ flat[base + lut]
                 for rho in range(128):
-                    y, x = ty * 128 + py * 8 + rho // 16, tx * 128 + px * 16 + rho % 16
+                    y, x = ty * 128 + py * r2 + rho // r1, tx * 128 + px * r1 + rho % r1
                     if y < H and x < W:
                         out[y, x] = col[rho]
     return out
 
 
-@pytest.mark.parametrize("bc,shape,r,t", [("periodic", "box", 1, 1), ("dirichlet", "star", 1, 1),
-                                          ("periodic", "box", 1, 2), ("periodic", "star", 3, 1)])
-def test_lut_emulation_reproduces_oracle_step(lib, oracle_mod, bc, shape, r, t):
+@pytest.mark.parametrize("bc,shape,r,t,r1", [("periodic", "box", 1, 1, 16), ("dirichlet", "star", 1, 1, 16),
+                                             ("periodic", "box", 1, 2, 16), ("periodic", "star", 3, 1, 16),
+                                             ("periodic", "box", 1, 1, 8), ("dirichlet", "star", 3, 1, 8),
+                                             ("periodic", "box", 1, 2, 8)])
+def test_lut_emulation_reproduces_oracle_step(lib, oracle_mod, bc, shape, r, t, r1):
     """Bit-level check of every table the kernel consumes: with exact dyadic weights the
     emulated sweep (LUT gather, permuted A'', patch map) equals t oracle steps exactly."""
     side = 2 * r + 1
     mask = inputs.stencil_mask(shape, 2, r)
     w = np.where(mask, np.arange(1, side * side + 1).reshape(side, side) / 256.0, 0.0).astype(np.float32)
     u = np.random.default_rng(3).integers(-8, 9, size=(140, 200)).astype(np.float64) / 8.0
-    plan = binding.Plan(w, u.shape, dtype="bf16", bc=bc, fusion_depth=t, shape=shape)
+    plan = binding.Plan(w, u.shape, dtype="bf16", bc=bc, fusion_depth=t, shape=shape, layout=(r1, -1))
     tb = plan.tables()
     dense = morph.decompress_2_4(tb["a_hi"].astype(np.float64) + tb["a_lo"], tb["a_idx"])
     ref = oracle_mod.run(u, w.astype(np.float64), bc, t)
@@ -205,7 +221,7 @@ def test_lut_emulation_reproduces_oracle_step(lib, oracle_mod, bc, shape, r, t):
         np.testing.assert_array_equal(got, ref)
     else:
         # fused weights are not exact in BF16: compare with the oracle at the weight rounding level
-        dense64 = morph.apply_permutation(morph.crushed_weights(tb["fused_w"], 16, 8), list(tb["order"]))
+        dense64 = morph.apply_permutation(morph.crushed_weights(tb["fused_w"], r1, 128 // r1), list(tb["order"]))
         got = _emulate_sweep(plan, tb, u, bc, dense64)
         np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
 
