@@ -206,25 +206,47 @@ constexpr int DWARPS = 4;  // warps per CTA
 
 __device__ __forceinline__ float f4c(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
 
-// The 4 + 2R values of one input row around the lane's four columns x .. x+3: s[R + j] is
-// column x + j (j = -R .. 3 + R).  row: the row's first element, or null for a row of zeros.
+// One input row's loads for a lane: its float4 at columns x .. x+3 and, at the warp's edges,
+// the R halo columns on each side that no neighbouring lane holds (zeros for a row of zeros:
+// row null).
 template <int R>
-__device__ __forceinline__ void row_window(const float* __restrict__ row, int64_t x, bool active, bool left_shfl,
-                                           bool right_shfl, int64_t xl, int64_t xr, float (&s)[4 + 2 * R]) {
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f), hl = v, hr = v;
+struct RowLoad {
+  float4 v;
+  float hl[R], hr[R];  // columns x-R .. x-1 and x+4 .. x+3+R
+};
+template <int R>
+__device__ __forceinline__ RowLoad<R> load_row(const float* __restrict__ row, int64_t x, bool active, bool left_shfl,
+                                               bool right_shfl, int64_t xl, int64_t xr) {
+  RowLoad<R> r;
+  r.v = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 hl = r.v, hr = r.v;
   if (row && active) {
-    v = *reinterpret_cast<const float4*>(row + x);
+    r.v = *reinterpret_cast<const float4*>(row + x);
     if (!left_shfl && xl >= 0) hl = *reinterpret_cast<const float4*>(row + xl);
     if (!right_shfl && xr >= 0) hr = *reinterpret_cast<const float4*>(row + xr);
   }
 #pragma unroll
-  for (int j = 0; j < 4; j++) s[R + j] = f4c(v, j);
+  for (int m = 0; m < R; m++) {
+    r.hl[m] = f4c(hl, 4 - R + m);
+    r.hr[m] = f4c(hr, m);
+  }
+  return r;
+}
+
+// The 4 + 2R values of one input row around the lane's four columns x .. x+3 (s[R + j] is
+// column x + j, j = -R .. 3 + R): the lane's own float4, R halo values from each neighbouring
+// lane by shuffle, or the edge values loaded by load_row.
+template <int R>
+__device__ __forceinline__ void row_values(const RowLoad<R>& r, bool left_shfl, bool right_shfl,
+                                           float (&s)[4 + 2 * R]) {
+#pragma unroll
+  for (int j = 0; j < 4; j++) s[R + j] = f4c(r.v, j);
 #pragma unroll
   for (int m = 0; m < R; m++) {
-    const float up = __shfl_up_sync(0xffffffffu, f4c(v, 3 - m), 1);
-    const float dn = __shfl_down_sync(0xffffffffu, f4c(v, m), 1);
-    s[R - 1 - m] = left_shfl ? up : f4c(hl, 3 - m);
-    s[R + 4 + m] = right_shfl ? dn : f4c(hr, m);
+    const float up = __shfl_up_sync(0xffffffffu, f4c(r.v, 4 - R + m), 1);
+    const float dn = __shfl_down_sync(0xffffffffu, f4c(r.v, m), 1);
+    s[m] = left_shfl ? up : r.hl[m];
+    s[R + 4 + m] = right_shfl ? dn : r.hr[m];
   }
 }
 
@@ -253,21 +275,22 @@ __global__ void __launch_bounds__(DWARPS * 32) direct2d_reg_kernel(const __grid_
   // input rows y0 - R .. y0 + nout + R - 1: each wraps at most once (H >= R)
   const int nout = (int)(H - y0 < seg ? H - y0 : seg);
   const int nrows = nout + 2 * R;
+  auto row_ptr = [&](int i) -> const float* {  // input row y0 - R + i, null for a row of zeros
+    int64_t r = y0 - R + i;
+    if (p.periodic) return in + (r < 0 ? r + H : (r >= H ? r - H : r)) * W;
+    return (r >= 0 && r < H) ? in + r * W : nullptr;
+  };
+  // the loads of the next input row are issued before this row's FMAs
+  RowLoad<R> next = load_row<R>(row_ptr(0), x, active, left_shfl, right_shfl, xl, xr);
   for (int ib = 0; ib < nrows; ib += K) {
 #pragma unroll
     for (int ii = 0; ii < K; ii++) {
       const int i = ib + ii;  // input row y0 - R + i
       if (i >= nrows) break;
-      int64_t r = y0 - R + i;
-      const float* row = nullptr;
-      if (p.periodic) {
-        r = r < 0 ? r + H : (r >= H ? r - H : r);
-        row = in + r * W;
-      } else if (r >= 0 && r < H) {
-        row = in + r * W;
-      }
+      const RowLoad<R> cur = next;
+      if (i + 1 < nrows) next = load_row<R>(row_ptr(i + 1), x, active, left_shfl, right_shfl, xl, xr);
       float s[4 + 2 * R];
-      row_window<R>(row, x, active, left_shfl, right_shfl, xl, xr, s);
+      row_values<R>(cur, left_shfl, right_shfl, s);
       // output row y0 + i - R - a takes this row through weight row a (a = -R .. R); its
       // accumulator slot is (i - R - a) mod K (compile-time: ib is a multiple of K)
 #pragma unroll
@@ -296,7 +319,7 @@ __global__ void __launch_bounds__(DWARPS * 32) direct2d_reg_kernel(const __grid_
 // rows y-1 .. y+D3ROWS of each.  STAR: only the 7 points of the star (the other weights are
 // zero), in the same order; two rows per warp (the dense cube keeps one, for registers).
 template <bool STAR, int D3ROWS = STAR ? 2 : 1>
-__global__ void __launch_bounds__(DWARPS * 32) direct3d_reg_kernel(const __grid_constant__ DirectParams p,
+__global__ void __launch_bounds__(DWARPS * 32, 4) direct3d_reg_kernel(const __grid_constant__ DirectParams p,
                                                                     const float* __restrict__ in,
                                                                     float* __restrict__ out) {
   constexpr int NR = D3ROWS + 2;  // input rows per plane
@@ -333,22 +356,33 @@ __global__ void __launch_bounds__(DWARPS * 32) direct3d_reg_kernel(const __grid_
   // input planes z0 - 1 .. z0 + nout: each wraps at most once
   const int nout = (int)(D - z0 < D3SEG ? D - z0 : D3SEG);
   const int npl = nout + 2;
+  auto load_plane = [&](int i, RowLoad<1> (&rl)[NR]) {  // input plane z0 - 1 + i
+    int64_t z = z0 - 1 + i;
+    bool zin = true;
+    if (p.periodic)
+      z = z < 0 ? z + D : (z >= D ? z - D : z);
+    else
+      zin = z >= 0 && z < D;
+#pragma unroll
+    for (int d = 0; d < NR; d++)
+      rl[d] = load_row<1>((zin && yin[d]) ? in + (z * H + ys[d]) * W : nullptr, x, active, left_shfl, right_shfl, xl,
+                          xr);
+  };
+  // the loads of the next input plane are issued before this plane's FMAs
+  RowLoad<1> next[NR];
+  load_plane(0, next);
   for (int ib = 0; ib < npl; ib += 3) {
 #pragma unroll
     for (int ii = 0; ii < 3; ii++) {
       const int i = ib + ii;  // input plane z0 - 1 + i
       if (i >= npl) break;
-      int64_t z = z0 - 1 + i;
-      bool zin = true;
-      if (p.periodic)
-        z = z < 0 ? z + D : (z >= D ? z - D : z);
-      else
-        zin = z >= 0 && z < D;
+      RowLoad<1> cur[NR];
+#pragma unroll
+      for (int d = 0; d < NR; d++) cur[d] = next[d];
+      if (i + 1 < npl) load_plane(i + 1, next);
       float s[NR][6];
 #pragma unroll
-      for (int d = 0; d < NR; d++)
-        row_window<1>((zin && yin[d]) ? in + (z * H + ys[d]) * W : nullptr, x, active, left_shfl, right_shfl, xl,
-                      xr, s[d]);
+      for (int d = 0; d < NR; d++) row_values<1>(cur[d], left_shfl, right_shfl, s[d]);
 #pragma unroll
       for (int a = -1; a <= 1; a++) {
         const int slot = ((ii - 1 - a) % 3 + 6) % 3;
@@ -619,6 +653,85 @@ __global__ void band2d_kernel(const BandParams p) {
 
 
 // ---------------------------------------------------------------------------------------
+// 3D Dirichlet frame of a fused radius-1 sweep of depth t: the cells within bw = t - 1 of a
+// face need step-by-step values (the fused kernel sees the zero boundary only once).  The
+// frame is cut into boxes: z slabs (z < bw or z >= D - bw, all y and x), y slabs (the other
+// z, y < bw or y >= H - bw), x slabs (the other z and y, x < bw or x >= W - bw), each cut into
+// chunks of up to kB3 x kB3 cells across.  A CTA stages its box widened by t cells (zeros
+// outside the grid), takes t FP32 steps in shared memory with the zero boundary re-imposed,
+// FMAs in (dz, dy, dx) order, and writes the box.
+// ---------------------------------------------------------------------------------------
+constexpr int kB3 = 32;
+
+__global__ void band3d_kernel(const Band3DParams p) {
+  allow_next_sweep();
+  extern __shared__ float b3[];
+  const int D = p.D, H = p.H, W = p.W, bw = p.bw, t = p.t;
+  const int zlo = bw < D ? bw : D, zhi0 = (D - bw > zlo) ? D - bw : zlo;  // z slabs [0, zlo), [zhi0, D)
+  const int ylo = bw < H ? bw : H, yhi0 = (H - bw > ylo) ? H - bw : ylo;
+  const int xlo = bw < W ? bw : W, xhi0 = (W - bw > xlo) ? W - bw : xlo;
+  int b = (int)blockIdx.x;
+  int z0, z1, y0, y1, x0, x1;
+  const int nz_slab = p.nzy * p.nzx, ny_slab = p.nyz * p.nyx, nx_slab = p.nxz * p.nxy;
+  if (b < 2 * nz_slab) {
+    const int s = b / nz_slab, c = b % nz_slab;
+    z0 = s ? zhi0 : 0, z1 = s ? D : zlo;
+    y0 = (c / p.nzx) * kB3, y1 = min(H, y0 + kB3), x0 = (c % p.nzx) * kB3, x1 = min(W, x0 + kB3);
+  } else if ((b -= 2 * nz_slab) < 2 * ny_slab) {
+    const int s = b / ny_slab, c = b % ny_slab;
+    z0 = zlo + (c / p.nyx) * kB3, z1 = min(zhi0, z0 + kB3);
+    y0 = s ? yhi0 : 0, y1 = s ? H : ylo;
+    x0 = (c % p.nyx) * kB3, x1 = min(W, x0 + kB3);
+  } else {
+    b -= 2 * ny_slab;
+    if (b >= 2 * nx_slab) return;
+    const int s = b / nx_slab, c = b % nx_slab;
+    z0 = zlo + (c / p.nxy) * kB3, z1 = min(zhi0, z0 + kB3);
+    y0 = ylo + (c % p.nxy) * kB3, y1 = min(yhi0, y0 + kB3);
+    x0 = s ? xhi0 : 0, x1 = s ? W : xlo;
+  }
+  if (z0 >= z1 || y0 >= y1 || x0 >= x1) return;
+  const int wz0 = z0 - t, wy0 = y0 - t, wx0 = x0 - t;
+  const int WD = z1 - z0 + 2 * t, WH = y1 - y0 + 2 * t, WW = x1 - x0 + 2 * t;
+  const int n = WD * WH * WW;
+  float* a = b3;
+  float* c = b3 + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int zz = i / (WH * WW), yy = (i / WW) % WH, xx = i % WW;
+    const int z = wz0 + zz, y = wy0 + yy, x = wx0 + xx;
+    a[i] = (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W)
+               ? p.src[(int64_t)(z + p.src_off) * p.src_plane + (int64_t)(y + p.src_off) * p.src_pitch + x + p.src_off]
+               : 0.f;
+  }
+  __syncthreads();
+  for (int s = 0; s < t; s++) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int zz = i / (WH * WW), yy = (i / WW) % WH, xx = i % WW;
+      const int z = wz0 + zz, y = wy0 + yy, x = wx0 + xx;
+      float v = 0.f;
+      if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W && zz >= 1 && zz < WD - 1 && yy >= 1 &&
+          yy < WH - 1 && xx >= 1 && xx < WW - 1) {
+        const float* q = a + ((zz - 1) * WH + (yy - 1)) * WW + (xx - 1);
+        for (int dz = 0; dz < 3; dz++)
+          for (int dy = 0; dy < 3; dy++)
+            for (int dx = 0; dx < 3; dx++) v = fmaf(p.w[(dz * 3 + dy) * 3 + dx], q[(dz * WH + dy) * WW + dx], v);
+      }
+      c[i] = v;
+    }
+    __syncthreads();
+    float* tmp = a;
+    a = c;
+    c = tmp;
+  }
+  const int bd = z1 - z0, bh = y1 - y0, bwid = x1 - x0;
+  for (int i = threadIdx.x; i < bd * bh * bwid; i += blockDim.x) {
+    const int z = z0 + i / (bh * bwid), y = y0 + (i / bwid) % bh, x = x0 + i % bwid;
+    p.dst[(int64_t)(z + p.dst_off) * p.dst_plane + (int64_t)(y + p.dst_off) * p.dst_pitch + x + p.dst_off] =
+        a[((z - wz0) * WH + (y - wy0)) * WW + (x - wx0)];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // 3D copy-in: unpadded D x H x W -> padded (D + 2G) x (H + 2G) x Wp; ghost cells hold the
 // periodic images or zeros; columns beyond W + 2G are zero.  One thread per padded cell.
 // ---------------------------------------------------------------------------------------
@@ -752,6 +865,27 @@ cudaError_t launch_band2d(BandParams p, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(band2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   band2d_kernel<<<blocks, 256, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band3d(Band3DParams p, cudaStream_t stream) {
+  if (p.t < 2 || p.bw <= 0) return cudaSuccess;
+  auto cdiv = [](int a, int b) { return a > 0 ? (a + b - 1) / b : 0; };
+  const int zmid = p.D - 2 * p.bw > 0 ? p.D - 2 * p.bw : 0, ymid = p.H - 2 * p.bw > 0 ? p.H - 2 * p.bw : 0;
+  p.nzy = cdiv(p.H, kB3);
+  p.nzx = cdiv(p.W, kB3);
+  p.nyz = cdiv(zmid, kB3);
+  p.nyx = cdiv(p.W, kB3);
+  p.nxz = cdiv(zmid, kB3);
+  p.nxy = cdiv(ymid, kB3);
+  const int blocks = 2 * (p.nzy * p.nzx + p.nyz * p.nyx + p.nxz * p.nxy);
+  // the largest box: bw x kB3 x kB3 (or kB3 x kB3 x kB3 when bw > kB3), widened by t per side
+  const int e = kB3 + 2 * p.t, thin = (p.bw < kB3 ? p.bw : kB3) + 2 * p.t;
+  const size_t smem = 2 * (size_t)e * e * thin * sizeof(float);
+  if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t err = cudaFuncSetAttribute(band3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  if (blocks > 0) band3d_kernel<<<blocks, 256, smem, stream>>>(p);
   return cudaGetLastError();
 }
 

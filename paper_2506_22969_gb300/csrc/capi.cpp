@@ -492,6 +492,7 @@ spst::Sweep2DParams sweep_params(sparstencil_plan_t p, const SweepTables& T, con
   prm.growth = p->growth;
   prm.status = status;
   prm.wait_ns = g_wait_ns;
+  prm.hstages = spst::sweep2d_halo_stages(prm);
   return prm;
 }
 
@@ -542,7 +543,27 @@ cudaError_t after_sweep(sparstencil_plan_t p, int depth, const float* src, const
     return spst::launch_ghost_refresh1d(prm.out, g.W, g.G, stream);
   }
   if (g.ndim == 3) {
-    if (last || p->bc != SPST_PERIODIC) return cudaSuccess;
+    if (p->bc == SPST_DIRICHLET_ZERO) {
+      if (depth < 2) return cudaSuccess;
+      spst::Band3DParams b;
+      std::memset(&b, 0, sizeof(b));
+      b.src = src;
+      b.src_pitch = g.Wp;
+      b.src_plane = g.Wp * g.Hp;
+      b.src_off = g.G;
+      b.dst = prm.out;
+      b.dst_pitch = prm.out_pitch;
+      b.dst_plane = prm.out_plane;
+      b.dst_off = prm.out_off;
+      b.D = (int)g.D;
+      b.H = (int)g.H;
+      b.W = (int)g.W;
+      b.t = depth;
+      b.bw = depth - 1;
+      for (size_t i = 0; i < p->w64.size() && i < 27; i++) b.w[i] = (float)p->w64[i];
+      return spst::launch_band3d(b, stream);
+    }
+    if (last) return cudaSuccess;
     return spst::launch_ghost_refresh3d(prm.out, (int)g.D, (int)g.H, (int)g.W, g.G, g.Wp, stream);
   }
   return launch_band(p, depth, src, prm.out, prm.out_pitch, prm.out_off, stream);
@@ -939,7 +960,7 @@ sparstencil_status enqueue_batch(const sparstencil_plan_t* plans, const float* c
   // kernel template of a job: FP16 or BF16, single or split words, dimensionality
   auto group = [&](int i) {
     return (word_of(plans[i]->dtype) == spst::Word::FP16 ? 1 : 0) + (is_split(plans[i]->dtype) ? 2 : 0) +
-           4 * plans[i]->geo.ndim;
+           4 * plans[i]->geo.ndim + (plans[i]->geo.ndim == 2 && plans[i]->geo.r1 == 8 ? 16 : 0);
   };
   std::vector<CUtensorMap> maps;
   std::vector<spst::Sweep2DParams> prms;
@@ -1038,15 +1059,19 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   p->bc = bc;
   p->requested_t = fusion_depth;
   p->t = fusion_depth == 0 ? 1 : fusion_depth;
-  if (bc == SPST_DIRICHLET_ZERO && p->t > 1 && (radius > 4 || ndim != 2))
-    return fail(SPST_ERR_UNSUPPORTED, "temporal fusion with a Dirichlet boundary needs a 2D grid and radius <= 4");
+  // Dirichlet fusion needs the exact frame of each sweep: the 2D band kernel (radius <= 4) or
+  // the 3D one (radius 1); 1D Dirichlet plans run one step per sweep
+  auto dirichlet_fusion_ok = [&]() { return (ndim == 2 && radius <= 4) || (ndim == 3 && radius == 1); };
+  if (bc == SPST_DIRICHLET_ZERO && p->t > 1 && !dirichlet_fusion_ok())
+    return fail(SPST_ERR_UNSUPPORTED,
+                "temporal fusion with a Dirichlet boundary needs a 2D grid with radius <= 4 or a 3D grid with radius 1");
   p->t_max = p->t;
   // fusion_depth 0: the deepest depth whose tables fit is planned (searched down from 6 in 2D,
   // 3 in 3D); the first run times the depths up to it and keeps the fastest per time step.
   // 1D: K grows by only 2r columns per fused step (k' = kt + 127), so the search starts at the
   // largest fused radius the tiles allow (60)
   const int t_deep = ndim == 1 ? std::max(1, 60 / radius) : ndim == 2 ? 6 : 3;
-  const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && (radius > 4 || ndim != 2)) ? 1 : t_deep) : p->t;
+  const int t_try = fusion_depth == 0 ? ((bc == SPST_DIRICHLET_ZERO && !dirichlet_fusion_ok()) ? 1 : t_deep) : p->t;
   const int side = 2 * radius + 1;
   p->w64.resize((size_t)side * (ndim >= 2 ? side : 1) * (ndim == 3 ? side : 1));
   for (size_t i = 0; i < p->w64.size(); i++) p->w64[i] = (double)weights[i];
@@ -1070,7 +1095,17 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
       probe.kchunks = p->full.kpad / 32;
       probe.a_pieces = p->full.a_pieces;
       probe.b_pieces = is_split(dtype) ? 2 : 1;
-      if (!spst::sweep2d_fits(probe)) err = "halo tile of the fused radius does not fit in shared memory";
+      if (spst::sweep2d_halo_stages(probe) == 0) err = "halo tile of the fused radius does not fit in shared memory";
+    }
+    if (err.empty() && fusion_depth == 0 && ndim == 3 && is_split(dtype) && tm > 1) {
+      // 3D split operands meet their tolerance over long runs only with the low-order
+      // accumulator (one accumulator: 1.0e-5 on 512^3 over 50 steps at t = 1, 2.1e-5 fused
+      // t = 2), so the search keeps the depths where it fits (for BF16, beside three pieces)
+      p->lo_acc = true;
+      SweepTables lo;
+      const bool lo_fits = build_tables(p.get(), tm, &lo).empty() && (dtype == SPST_FP16_SPLIT || lo.a_pieces == 3);
+      p->lo_acc = false;
+      if (!lo_fits) err = "the low-order accumulator does not fit at this depth";
     }
     if (err.empty() || fusion_depth != 0) break;
   }
@@ -1118,7 +1153,7 @@ sparstencil_status sparstencil_plan_set_layout(sparstencil_plan_t plan, int r1, 
   if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
   if (!plan->dev_tables.empty()) return fail(SPST_ERR_INVALID, "set the layout before the plan's first run");
   if (pairing < -1 || pairing > 1) return fail(SPST_ERR_INVALID, "pairing must be -1, 0 or 1");
-  if (plan->geo.ndim == 2 ? (r1 != 16 && r1 != 8) : r1 != plan->geo.r1)
+  if (plan->geo.ndim == 2 ? (r1 != 16 && r1 != 8) : r1 != plan->full.r1)
     return fail(SPST_ERR_UNSUPPORTED, plan->geo.ndim == 2 ? "2D patches are 16 x 8 (r1 = 16) or 8 x 16 (r1 = 8)"
                                                           : "1D and 3D plans have one patch shape");
   const std::string err = apply_layout(plan, Layout{r1, (spst::Pairing)pairing});

@@ -40,6 +40,7 @@ struct Sweep2DParams {
                         // (128 columns after the main one) that the epilogue adds in FP32; nacc = 1
   int nslots;           // B'' chunk slots in shared memory (1..kMaxBSlots; set by launch_sweep2d)
   int early_tma;        // 1: tile 0's halo load is issued before the set-up (set by launch_sweep2d)
+  int hstages;          // halo tile stages in shared memory: 2 (the next tile loads during the gather) or 1
   int fp16;             // operand type: 1 = FP16, 0 = BF16
   float wscale;         // 2^-s: the weight pieces hold w * 2^s
   const int32_t* lut;         // [kpad] tile-word offsets (device)
@@ -82,9 +83,11 @@ cudaError_t launch_sweep2d_multi(const CUtensorMap* maps, const Sweep2DParams* p
 size_t sweep2d_smem_bytes(const Sweep2DParams& p);
 // Largest chunk-slot count (<= kMaxBSlots) that fits the per-CTA shared memory, or 0.
 int sweep2d_max_slots(const Sweep2DParams& p);
-// Whether the sweep kernel fits shared memory for this geometry (halo stages, >= 2 chunk
-// slots, and the set-up staging of A'' and the metadata).
+// Whether the sweep kernel fits shared memory for this geometry (p.hstages halo stages,
+// >= 2 chunk slots, and the set-up staging of A'' and the metadata).
 bool sweep2d_fits(const Sweep2DParams& p);
+// Halo stages for this geometry: 2 where they fit beside the chunk slots, else 1, else 0.
+int sweep2d_halo_stages(const Sweep2DParams& p);
 // Whether launch_sweep2d lets a sweep overlap its set-up with the previous kernel
 // (programmatic dependent launch; on by default, per host thread).
 void sweep2d_set_programmatic_launch(bool on);
@@ -141,6 +144,22 @@ struct BandParams {
   float w[81];            // single-step weights, dense (2r+1)^2 [dy][dx], r <= 4
 };
 cudaError_t launch_band2d(BandParams p, cudaStream_t stream);
+
+// 3D, radius 1: the Dirichlet frame of width bw = t - 1 on the six faces of a fused sweep of
+// depth t >= 2, recomputed step by step in FP32 from the sweep's input.
+struct Band3DParams {
+  const float* src;       // the sweep's input grid (padded: ghost width src_off, zeros outside)
+  int64_t src_pitch, src_plane;
+  int src_off;
+  float* dst;             // the sweep's output grid (frame cells overwritten)
+  int64_t dst_pitch, dst_plane;
+  int dst_off;
+  int D, H, W;
+  int t, bw;
+  int nzx, nzy, nyz, nyx, nxz, nxy;  // chunk counts of the z, y and x slabs (set by launch_band3d)
+  float w[27];            // single-step weights, dense 3 x 3 x 3 [dz][dy][dx]
+};
+cudaError_t launch_band3d(Band3DParams p, cudaStream_t stream);
 
 // FP64 norms of x against ref (see sparstencil_error_norms); acc: 4 doubles of device memory.
 cudaError_t launch_error_norms(const float* x, const float* ref, int64_t n, double* acc, cudaStream_t stream);

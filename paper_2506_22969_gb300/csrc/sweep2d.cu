@@ -288,7 +288,7 @@ struct SmemLayout {
   __host__ __device__ explicit SmemLayout(const Sweep2DParams& p) {
     uint32_t halo = (uint32_t)p.box_d * (uint32_t)p.box_h * (uint32_t)p.P * 4u;
     halo_stride = (halo + 1023u) & ~1023u;
-    off_b = halo_stride * kHaloStages;
+    off_b = halo_stride * (uint32_t)(p.hstages == 1 ? 1 : kHaloStages);
     slot_bytes = (uint32_t)p.b_pieces * (uint32_t)kPieceBytes;
     off_lut = off_b + slot_bytes * (uint32_t)p.nslots;
     off_cv = off_lut + (((uint32_t)p.kpad * 4u + 15u) & ~15u);
@@ -318,10 +318,11 @@ constexpr int kItems = 64 / kGatherWarps;                        // patch pairs 
 // patches n and n+8, 16 words apart in x, as in 2D.
 // The sweep of one grid by CTA `cta` of the `ncta` CTAs given to it: tiles cta, cta + ncta, ...
 // tmap_in: the TMA map of the input padded grid (kernel parameter space).
-template <int FP16, int SPLIT, int DIM>
+template <int FP16, int SPLIT, int DIM, int TALL>
 __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Sweep2DParams& p, const int cta,
                                            const int ncta) {
   constexpr bool DIM3 = DIM == 3, DIM1 = DIM == 1;
+  constexpr bool kTall = DIM == 2 && TALL != 0;  // 2D 8 x 16 patches (compiled apart: the 16 x 8 path is unchanged)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -453,6 +454,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Swe
 
   const int ntiles_cta = (p.num_tiles > cta) ? (p.num_tiles - 1 - cta) / ncta + 1 : 0;
   const bool tr = (blockIdx.x == 0) && g_trace_on;
+  const bool hs2 = p.hstages != 1;  // two halo stages (one: the next tile loads after this one's gather)
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -460,8 +462,10 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Swe
       const uint32_t bytes = (uint32_t)p.box_d * (uint32_t)p.box_h * (uint32_t)p.P * 4u;
       int issued = 0;
       for (int li = 0; li < ntiles_cta; li++) {
-        const int stage = li & 1;
-        if (li >= 2 && !mbar_wait(bar(BAR_HEMPTY + stage), ((li >> 1) - 1) & 1, wait_ns, abort_flag, p.status)) break;
+        // halo stage and the number of its earlier uses (two stages, or one when the fused
+        // radius leaves room for a single halo tile only)
+        const int stage = hs2 ? li & 1 : 0, use = hs2 ? li >> 1 : li;
+        if (use >= 1 && !mbar_wait(bar(BAR_HEMPTY + stage), (use - 1) & 1, wait_ns, abort_flag, p.status)) break;
         const int tt = cta + li * ncta;
         const uint32_t dst = sbase + (uint32_t)stage * L.halo_stride;
         trace(tr, 0, li, 0);
@@ -490,9 +494,10 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Swe
         }
         issued++;
       }
-      // the CTA never exits with one of its copies in flight (at most the last two can be)
-      for (int li = (issued > 2 ? issued - 2 : 0); li < issued; li++)
-        mbar_wait(bar(BAR_HFULL + (li & 1)), (li >> 1) & 1, kDrainNs, nullptr, p.status);
+      // the CTA never exits with one of its copies in flight (at most the last one per stage can be)
+      const int nst = hs2 ? 2 : 1;
+      for (int li = (issued > nst ? issued - nst : 0); li < issued; li++)
+        mbar_wait(bar(BAR_HFULL + (hs2 ? li & 1 : 0)), (hs2 ? li >> 1 : li) & 1, kDrainNs, nullptr, p.status);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -599,8 +604,8 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Swe
     // row rho of a patch: 2D (ry, rx) = (rho / 16, rho % 16); 3D (rz, ry, rx) = (rho / 32,
     // rho / 8 % 4, rho % 8)
     const int rz = DIM3 ? rho >> 5 : 0;
-    const int ry = DIM3 ? (rho >> 3) & 3 : (p.tall ? rho >> 3 : rho >> 4);
-    const int rx = DIM3 ? rho & 7 : (p.tall ? rho & 7 : rho & 15);
+    const int ry = DIM3 ? (rho >> 3) & 3 : (kTall ? rho >> 3 : rho >> 4);
+    const int rx = DIM3 ? rho & 7 : (kTall ? rho & 7 : rho & 15);
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
     const uint32_t cv_s = sbase + L.off_cv;
     const float out_scale = p.wscale * dscale_inv;  // undoes the weight and data scales (powers of two)
@@ -725,9 +730,11 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Swe
         // column cg*16 + j is the patch whose outputs start yoff rows and xoff columns into
         // the tile: 16 x 8 patches (py, px) = (cg/4*8 + j%8, (2cg + j/8) % 8); tall 8 x 16
         // patches (py, px) = (cg, 4((j%8)/2) + 2(j/8) + j%2)
-        auto yoff = [&](int j) { return p.tall ? cg * 16 : (((cg >> 2) << 3) + (j & 7)) * 8; };
-        auto xoff = [&](int j) { return p.tall ? (4 * ((j & 7) >> 1) + 2 * (j >> 3) + (j & 1)) * 8 : (((2 * cg) & 7) + (j >> 3)) * 16; };
-        if (full && !p.tall) {
+        auto yoff = [&](int j) { return kTall ? cg * 16 : (((cg >> 2) << 3) + (j & 7)) * 8; };
+        auto xoff = [&](int j) {
+          return kTall ? (4 * ((j & 7) >> 1) + 2 * (j >> 3) + (j & 1)) * 8 : (((2 * cg) & 7) + (j >> 3)) * 16;
+        };
+        if (full && !kTall) {
           const int py0 = (cg >> 2) << 3, px0 = (2 * cg) & 7;
 #pragma unroll
           for (int j = 0; j < 16; j++) obase[(int64_t)(py0 + (j & 7)) * pitch8 + (px0 + (j >> 3)) * 16] = val[j];
@@ -789,7 +796,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Swe
         const int a = n >> 4, b = n & 7;
         const int px = ((a & 1) << 2) | (h << 1) | (b & 1), py = b >> 1, pz = a >> 1;
         base_i[i] = 4 * (pz * 4 * p.box_h * P + py * 4 * P + px * 8);
-      } else if (p.tall) {
+      } else if (kTall) {
         // 8 x 16 patches: column n = 16 py + 8 hb + e is patch (px, py) = (4(e>>1) + 2hb + (e&1),
         // n >> 4), so the half-warps' patches (hb = h) are two patches, 16 words, apart in x
         const int e = n & 7, hb = (n >> 3) & 1;
@@ -809,8 +816,8 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Swe
         4u * (uint32_t)(DIM1 ? sm
                              : DIM3 ? (sm >> 2) * p.box_h * P + ((sm >> 1) & 1) * P + (sm & 1) : (sm >> 2) * P + (sm & 3));
     for (int li = 0; li < ntiles_cta; li++) {
-      const int stage = li & 1;
-      if (!warp_wait(bar(BAR_HFULL + stage), (li >> 1) & 1, wait_ns, abort_flag, p.status)) break;
+      const int stage = hs2 ? li & 1 : 0;
+      if (!warp_wait(bar(BAR_HFULL + stage), (hs2 ? li >> 1 : li) & 1, wait_ns, abort_flag, p.status)) break;
       trace(tr && gw == 0 && lane == 0, 2, li, 0);
       const uint32_t tile_s = sbase + (uint32_t)stage * L.halo_stride;
       uint32_t ba[kItems];
@@ -829,7 +836,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Swe
         // the same two partial sums, and FP32 addition is commutative).
         const uint32_t m0 = ba[i] + 4u * (uint32_t)(DIM1 ? G + 60
                                                          : DIM3 ? (G + 1) * p.box_h * P + (G + 1) * P + G + 3
-                                                                : p.tall ? (G + 7) * P + G + 2 : (G + 3) * P + G + 6);
+                                                                : kTall ? (G + 7) * P + G + 2 : (G + 3) * P + G + 6);
         float cs = lds_f32(m0 + c_off);
         cs += __shfl_xor_sync(0xffffffffu, cs, 1);
         cs += __shfl_xor_sync(0xffffffffu, cs, 2);
@@ -935,20 +942,20 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap* tmap_in, const Swe
 }
 
 // One grid per launch: every CTA takes its share of the grid's tiles.
-template <int FP16, int SPLIT, int DIM>
+template <int FP16, int SPLIT, int DIM, int TALL = 0>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep2d_kernel(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant__ Sweep2DParams p) {
-  sweep_body<FP16, SPLIT, DIM>(&tmap_in, p, (int)blockIdx.x, (int)gridDim.x);
+  sweep_body<FP16, SPLIT, DIM, TALL>(&tmap_in, p, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // Many grids per launch (a batch's sweeps of one index): CTA b works on job cta_job[b], as CTA
 // b - cta_first[job] of the cta_count[job] CTAs given to that job, with the job's own tables,
 // tensor map and output; a CTA never changes job, so its set-up (TMEM tables, lookup table)
 // is the single-grid one.
-template <int FP16, int SPLIT, int DIM>
+template <int FP16, int SPLIT, int DIM, int TALL = 0>
 __global__ void __launch_bounds__(kSweepThreads, 1) sweep2d_multi_kernel(const __grid_constant__ MultiSweepParams m) {
   const int j = m.cta_job[blockIdx.x];
-  sweep_body<FP16, SPLIT, DIM>(&m.tmap[j], m.job[j], (int)blockIdx.x - m.cta_first[j], m.cta_count[j]);
+  sweep_body<FP16, SPLIT, DIM, TALL>(&m.tmap[j], m.job[j], (int)blockIdx.x - m.cta_first[j], m.cta_count[j]);
 }
 
 }  // namespace
@@ -992,6 +999,15 @@ int sweep2d_max_slots(const Sweep2DParams& p) {
   return 0;
 }
 
+int sweep2d_halo_stages(const Sweep2DParams& p_in) {
+  Sweep2DParams p = p_in;
+  for (int s = kHaloStages; s >= 1; s--) {
+    p.hstages = s;
+    if (sweep2d_fits(p)) return s;
+  }
+  return 0;
+}
+
 bool sweep2d_fits(const Sweep2DParams& p_in) {
   Sweep2DParams p = p_in;
   p.nslots = sweep2d_max_slots(p);
@@ -1016,14 +1032,28 @@ bool finish_params(Sweep2DParams* p) {
   return need <= (size_t)L.off_lut;
 }
 
-template <typename K>
-K pick_kernel(const Sweep2DParams& p, K k100, K k110, K k103, K k113, K k101, K k111, K k000, K k010, K k003,
-              K k013, K k001, K k011) {
-  // naming: k<fp16><split><dim>, dim 0 = 2D
-  if (p.dim3) return p.fp16 ? (p.b_pieces > 1 ? k113 : k103) : (p.b_pieces > 1 ? k013 : k003);
-  if (p.dim1) return p.fp16 ? (p.b_pieces > 1 ? k111 : k101) : (p.b_pieces > 1 ? k011 : k001);
-  return p.fp16 ? (p.b_pieces > 1 ? k110 : k100) : (p.b_pieces > 1 ? k010 : k000);
+// The kernel instance of a sweep's template parameters (operand word, split, dimensionality,
+// 2D patch shape).
+using SingleKernel = void (*)(const CUtensorMap, const Sweep2DParams);
+using MultiKernel = void (*)(const MultiSweepParams);
+template <template <int, int, int, int> class Sel>
+typename Sel<0, 0, 2, 0>::type pick_kernel(const Sweep2DParams& p) {
+  const bool s = p.b_pieces > 1;
+  if (p.dim3) return p.fp16 ? (s ? Sel<1, 1, 3, 0>::get() : Sel<1, 0, 3, 0>::get()) : (s ? Sel<0, 1, 3, 0>::get() : Sel<0, 0, 3, 0>::get());
+  if (p.dim1) return p.fp16 ? (s ? Sel<1, 1, 1, 0>::get() : Sel<1, 0, 1, 0>::get()) : (s ? Sel<0, 1, 1, 0>::get() : Sel<0, 0, 1, 0>::get());
+  if (p.tall) return p.fp16 ? (s ? Sel<1, 1, 2, 1>::get() : Sel<1, 0, 2, 1>::get()) : (s ? Sel<0, 1, 2, 1>::get() : Sel<0, 0, 2, 1>::get());
+  return p.fp16 ? (s ? Sel<1, 1, 2, 0>::get() : Sel<1, 0, 2, 0>::get()) : (s ? Sel<0, 1, 2, 0>::get() : Sel<0, 0, 2, 0>::get());
 }
+template <int A, int B, int C, int D>
+struct SelSingle {
+  using type = SingleKernel;
+  static type get() { return sweep2d_kernel<A, B, C, D>; }
+};
+template <int A, int B, int C, int D>
+struct SelMulti {
+  using type = MultiKernel;
+  static type get() { return sweep2d_multi_kernel<A, B, C, D>; }
+};
 }  // namespace
 
 cudaError_t launch_sweep2d_multi(const CUtensorMap* maps, const Sweep2DParams* prm, int njobs, int num_sms,
@@ -1041,6 +1071,7 @@ cudaError_t launch_sweep2d_multi(const CUtensorMap* maps, const Sweep2DParams* p
     if (m.job[j].fp16 != prm[0].fp16 || m.job[j].b_pieces != prm[0].b_pieces || m.job[j].dim3 != prm[0].dim3 ||
         m.job[j].dim1 != prm[0].dim1)
       return cudaErrorInvalidValue;
+    if (m.job[j].tall != prm[0].tall) return cudaErrorInvalidValue;
     const size_t s = sweep2d_smem_bytes(m.job[j]);
     smem = s > smem ? s : smem;
     total_tiles += m.job[j].num_tiles;
@@ -1071,11 +1102,7 @@ cudaError_t launch_sweep2d_multi(const CUtensorMap* maps, const Sweep2DParams* p
     next += m.cta_count[j];
   }
   m.nctas = next;
-  auto kern = pick_kernel(m.job[0], sweep2d_multi_kernel<1, 0, 2>, sweep2d_multi_kernel<1, 1, 2>,
-                          sweep2d_multi_kernel<1, 0, 3>, sweep2d_multi_kernel<1, 1, 3>, sweep2d_multi_kernel<1, 0, 1>,
-                          sweep2d_multi_kernel<1, 1, 1>, sweep2d_multi_kernel<0, 0, 2>, sweep2d_multi_kernel<0, 1, 2>,
-                          sweep2d_multi_kernel<0, 0, 3>, sweep2d_multi_kernel<0, 1, 3>, sweep2d_multi_kernel<0, 0, 1>,
-                          sweep2d_multi_kernel<0, 1, 1>);
+  const MultiKernel kern = pick_kernel<SelMulti>(m.job[0]);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1102,12 +1129,7 @@ cudaError_t launch_sweep2d(const CUtensorMap& tmap_in, const Sweep2DParams& p_in
     if (need > (size_t)L.off_lut) return cudaErrorInvalidConfiguration;
   }
   const size_t smem = sweep2d_smem_bytes(p);
-  auto kern = p.dim3   ? (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 3> : sweep2d_kernel<1, 0, 3>)
-                                 : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 3> : sweep2d_kernel<0, 0, 3>))
-              : p.dim1 ? (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 1> : sweep2d_kernel<1, 0, 1>)
-                                 : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 1> : sweep2d_kernel<0, 0, 1>))
-                       : (p.fp16 ? (p.b_pieces > 1 ? sweep2d_kernel<1, 1, 2> : sweep2d_kernel<1, 0, 2>)
-                                 : (p.b_pieces > 1 ? sweep2d_kernel<0, 1, 2> : sweep2d_kernel<0, 0, 2>));
+  const SingleKernel kern = pick_kernel<SelSingle>(p);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;

@@ -106,6 +106,8 @@ CONFIGS = {
                          recipe="random", dims=(4096, 4096), steps=100, bc="periodic", grid="u01", seed=2),
     "heat3d_512": dict(name="Heat-3D 7-point star 512^3, Dirichlet zero, 50 steps", shape="star", ndim=3, radius=1,
                        recipe="random", dims=(512, 512, 512), steps=50, bc="dirichlet", grid="upm1", seed=3),
+    "heat3d_256": dict(name="Heat-3D 7-point star 256^3, Dirichlet zero", shape="star", ndim=3, radius=1,
+                       recipe="random", dims=(256, 256, 256), steps=50, bc="dirichlet", grid="upm1", seed=3),
     "box3d27p_256": dict(name="Box-3D 27-point 256^3, Dirichlet zero, 50 steps", shape="box", ndim=3, radius=1,
                          recipe="random", dims=(256, 256, 256), steps=50, bc="dirichlet", grid="upm1", seed=3),
     "star2d13p_8192": dict(name="Star-2D 13-point 8192^2, 200 steps", shape="star", ndim=2, radius=3,

@@ -12,7 +12,9 @@ the oracle's full-grid run (Sec. 2.2 iterated T times in FP64):
     remainder sweep of 4) in BF16 split;
   * Box-2D49P 8192^2, periodic, t = 2 (4096 tiles, 27 per CTA): 4 steps (two sweeps);
   * Box-3D27P 256^3, zero Dirichlet boundary, t = 1 (1024 tiles of 64 x 16 x 16): 3 steps;
-  * Heat-1D 10,240,000, periodic, t = 60 (625 tiles of 16384): 120 steps (two sweeps).
+  * Heat-1D 10,240,000, periodic, t = 60 (625 tiles of 16384): 120 steps (two sweeps);
+  * Heat-3D 7-point star 256^3, zero Dirichlet boundary, t = 2 (1024 tiles, one halo stage,
+    the 3D band kernel for the frame): 4 steps (two sweeps).
 
 Bounds (the same as every other parity test): rel-L2 <= 2e-3 for single 16-bit words and
 1e-5 for split words (the stated tolerances), and rel-Linf = max|x - ref| / max|ref| <= ten
@@ -65,6 +67,8 @@ def _case(oracle_mod, name, steps):
     ("box3d27p_256", 3, "bf16_split", 1),
     ("box3d27p_256", 3, "fp16", 1),
     ("heat1d", 120, "bf16_split", 60),
+    ("heat3d_256", 4, "fp16", 2),
+    ("heat3d_256", 4, "bf16_split", 2),
 ])
 def test_whole_grid_matches_oracle(torch_cuda, oracle_mod, name, steps, dtype, t):
     torch = torch_cuda

@@ -412,6 +412,25 @@ def test_sparse_3d_matches_oracle(torch_cuda, oracle_mod, shape, recipe, dims, s
     _assert_tol(l2, linf, dtype)
 
 
+@pytest.mark.parametrize("dims,steps,bc,dtype", [
+    ((34, 50, 130), 7, "dirichlet", "fp16"),         # fused sweeps, a remainder sweep, the 3D band
+    ((34, 50, 130), 7, "dirichlet", "bf16_split"),
+    ((40, 36, 72), 6, "periodic", "bf16"),           # ghost shell of width 2
+    ((17, 20, 66), 5, "periodic", "fp16_split"),
+])
+def test_sparse_3d_fused_matches_oracle(torch_cuda, oracle_mod, dims, steps, bc, dtype):
+    """3D radius-1 star fused two steps per sweep (one halo stage in shared memory); zero
+    Dirichlet boundaries take the frame of width 1 from the 3D band kernel."""
+    w = inputs.stencil_weights("star", 3, 1, "random", seed=12)
+    u = inputs.uniform_pm1(6, dims)
+    ref = oracle_mod.run(u, w, bc, steps)
+    got, plan = _run_sparse(torch_cuda, u, w, steps, dtype, bc, 2, "star")
+    assert plan.info().fusion_depth == 2
+    l2, linf = oracle_mod.rel_errors(got, ref)
+    assert np.all(np.isfinite(got))
+    _assert_tol(l2, linf, dtype)
+
+
 def test_full_size_box3d27p_sampled(torch_cuda, oracle_mod):
     """Box-3D27P 256^3, zero Dirichlet boundary, 50 steps, split operands: sampled points
     against the dependence-cone oracle."""

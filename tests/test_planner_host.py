@@ -300,6 +300,42 @@ def test_autotune_plan_takes_the_deepest_depth_that_fits(lib):
     w3 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=2)
     p3 = binding.Plan(w3, (512, 512), dtype="bf16_split", bc="periodic", fusion_depth=0)
     assert p3.info().fusion_depth == 2 and p3.info().mma_terms == 3
+    # 3D radius 1: the 7-point star fuses two steps (K_pad 512, one halo stage of 68 x 20 x 20
+    # floats), also with a zero Dirichlet boundary (the 3D band kernel); the 27-point box needs
+    # K_pad >= 768 at t = 2 and stays at t = 1
+    w7 = inputs.stencil_weights("star", 3, 1, "random", seed=2)
+    for bc in ("dirichlet", "periodic"):
+        p7 = binding.Plan(w7, (64, 64, 64), dtype="fp16", bc=bc, fusion_depth=0, shape="star")
+        assert p7.info().fusion_depth == 2 and p7.info().kpad == 512 and p7.info().ghost == 2
+    w27 = inputs.stencil_weights("box", 3, 1, "random", seed=2)
+    assert binding.Plan(w27, (64, 64, 64), dtype="fp16", bc="dirichlet", fusion_depth=0).info().fusion_depth == 1
+    # 3D split operands keep the depths where the low-order accumulator fits (t = 1 here)
+    for dt in ("fp16_split", "bf16_split"):
+        ps = binding.Plan(w7, (64, 64, 64), dtype=dt, bc="dirichlet", fusion_depth=0, shape="star")
+        assert ps.info().fusion_depth == 1 and ps.info().low_accumulator == 1
+
+
+def test_layout_setting(lib):
+    """sparstencil_plan_set_layout: 2D patches 16 x 8 or 8 x 16, pairings -1 / 0 / 1; other
+    shapes and 1D/3D shapes are refused and leave the plan unchanged."""
+    w = inputs.stencil_weights("star", 2, 3, "gaussian", seed=2)
+    p = binding.Plan(w, (300, 260), dtype="bf16", bc="periodic", fusion_depth=1, shape="star")
+    assert (p.info().r1, p.info().r2) == (16, 8)
+    p.set_layout(8, 0)
+    assert (p.info().r1, p.info().r2, p.info().pairing) == (8, 16, 0)
+    p.set_layout(8, 1)
+    assert p.info().pairing == 1
+    for r1, pairing, code in ((12, -1, 2), (16, 3, 1)):
+        with pytest.raises(binding.SparStencilError) as e:
+            p.set_layout(r1, pairing)
+        assert e.value.code == code
+    assert (p.info().r1, p.info().pairing) == (8, 1)
+    w3 = inputs.stencil_weights("box", 3, 1, "random", seed=2)
+    p3 = binding.Plan(w3, (32, 32, 64), dtype="bf16", bc="periodic", fusion_depth=1)
+    with pytest.raises(binding.SparStencilError) as e:
+        p3.set_layout(16, -1)
+    assert e.value.code == 2
+    p3.set_layout(8, -1)
 
 
 def test_low_accumulator_setting(lib):
