@@ -70,10 +70,11 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _profile_traffic(depth: int, profile: str = "sweep2d_box49_8192.md"):
+def _profile_traffic(depth: int, profile: str = "sweep2d_box49_8192.md", patch: int = 16):
     """Per-launch DRAM bytes of the sweep kernel from a committed ncu summary, if the summary
     was taken on the current kernel source (sweep2d.cu + kernels.h) at the timed fusion depth
-    (else None)."""
+    and 2D patch shape (else None).  A summary may list one figure per patch shape
+    ('dram_bytes_per_launch_scaled_patch8:' for 8 x 16 patches)."""
     csrc = os.path.join(ROOT, "paper_2506_22969_gb300", "csrc")
     prof = os.path.join(ROOT, "profiles", profile)
     try:
@@ -85,7 +86,8 @@ def _profile_traffic(depth: int, profile: str = "sweep2d_box49_8192.md"):
         with open(prof) as f:
             text = f.read()
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
-        m_tr = re.search(r"dram_bytes_per_launch_scaled:\s*([0-9.eE+]+)", text)
+        key = "dram_bytes_per_launch_scaled" + ("" if patch == 16 else f"_patch{patch}")
+        m_tr = re.search(key + r":\s*([0-9.eE+]+)", text)
         m_t = re.search(r"fusion_depth:\s*([0-9]+)", text)
         if m_sha and m_tr and m_t and m_sha.group(1) == sha and int(m_t.group(1)) == depth:
             return float(m_tr.group(1))
@@ -232,10 +234,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def ncu_case(spec: str, t: int):
+def ncu_case(spec: str, t: int, patch: int = 16):
     """Small profiling case: 3 runs of one fused sweep each (copy-in + 1 sweep kernel).
     spec = '<workload>:<precision>[:<side>]', e.g. 'box2d49p_8192:bf16_split' (side: a
-    side x side grid instead of the workload's)."""
+    side x side grid instead of the workload's); patch: the 2D patch shape (16: 16 x 8,
+    8: 8 x 16)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -248,7 +251,8 @@ def ncu_case(spec: str, t: int):
         u = np.ascontiguousarray(u[:side, :side])
     x = torch.from_numpy(u).cuda()
     y = torch.empty_like(x)
-    plan = binding.Plan(w, u.shape, dtype=prec, bc=cfg["bc"], fusion_depth=t, shape=cfg["shape"])
+    plan = binding.Plan(w, u.shape, dtype=prec, bc=cfg["bc"], fusion_depth=t, shape=cfg["shape"],
+                        layout=(patch, -1) if u.ndim == 2 else None)
     for _ in range(3):
         plan.run(x, y, t)
     torch.cuda.synchronize()
@@ -351,6 +355,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="leave out the C5 serving trace")
     ap.add_argument("--no-variants", action="store_true", help="leave out the variant workloads")
     ap.add_argument("--fusion", type=int, default=0, help="fusion depth t (0: autotune)")
+    ap.add_argument("--patch", type=int, default=16, help="--ncu-case: 2D patch shape (16: 16 x 8, 8: 8 x 16)")
     ap.add_argument("--trace", action="store_true",
                     help="print the sweep kernel's CTA-0 timeline for single sweeps of the workload and exit")
     ap.add_argument("--ncu-case", default=None,
@@ -378,7 +383,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.ncu_case:
-        return ncu_case(args.ncu_case, args.fusion or 1)
+        return ncu_case(args.ncu_case, args.fusion or 1, args.patch)
     if args.trace:
         return trace_case()
 
@@ -490,7 +495,7 @@ def main():
     alg_bytes = 8.0 * H * W  # read 4 B + write 4 B per output per sweep
     achieved = alg_bytes / (sweep_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _profile_traffic(t_best)
+    traffic = _profile_traffic(t_best, patch=info.r1)
 
     # e2e through the host-buffer entry point (pinned), copies inside the timed region
     hx = torch.from_numpy(u).pin_memory()
