@@ -262,29 +262,43 @@ def ncu_case(spec: str, t: int, patch: int = 16):
 def ncu_kernels_case():
     """Profiling case covering every kernel of the library once or twice, each on inputs larger
     than L2 where the kernel streams a grid: the 3D sweep (Heat-3D 384^3, FP16, with its copy-in
-    and, periodic, its ghost refresh), the 1D sweep (Heat-1D 2^26, BF16 split, t = 8), the
-    Dirichlet band of a fused 2D sweep (Heat-2D 8192^2, t = 3), the FP32 direct kernels (1D,
-    2D radius 1 and 3, 3D radius 1) and the FP64 error norms."""
+    and, periodic, its ghost refresh; fused two steps with a zero Dirichlet boundary, with the
+    3D band), the 1D sweep (Heat-1D 2^26, BF16 split, t = 8, two sweeps with the ghost refresh
+    between them), the 2D sweep with 8 x 16 patches
+    and the Dirichlet band of a fused 2D sweep (Heat-2D 8192^2, t = 3), a batch launch of four
+    grids, the FP32 direct kernels (1D, 2D radius 1 and 3, 3D radius-1 star and box) and the
+    FP64 error norms."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2506_22969_gb300 import binding, inputs
-    cases = [("star", 3, 1, "random", (384, 384, 384), "fp16", "periodic", 1, 1),
-             ("star", 1, 1, "heat", (1 << 26,), "bf16_split", "periodic", 8, 8),
-             ("star", 2, 1, "heat", (8192, 8192), "bf16", "dirichlet", 3, 3)]
-    for shape, nd, r, recipe, dims, dt, bc, t, steps in cases:
+    cases = [("star", 3, 1, "random", (384, 384, 384), "fp16", "periodic", 1, 2, None),
+             ("star", 3, 1, "random", (384, 384, 384), "fp16", "dirichlet", 2, 2, None),
+             ("star", 1, 1, "heat", (1 << 26,), "bf16_split", "periodic", 8, 16, None),
+             ("star", 2, 1, "heat", (8192, 8192), "bf16", "dirichlet", 3, 3, (8, -1))]
+    for shape, nd, r, recipe, dims, dt, bc, t, steps, layout in cases:
         w = inputs.stencil_weights(shape, nd, r, recipe, seed=1)
         x = torch.from_numpy(inputs.uniform01(1, dims)).cuda()
         y = torch.empty_like(x)
-        plan = binding.Plan(w, dims, dtype=dt, bc=bc, fusion_depth=t, shape=shape)
+        plan = binding.Plan(w, dims, dtype=dt, bc=bc, fusion_depth=t, shape=shape, layout=layout)
         plan.run(x, y, steps)
         binding.direct_run(w, x, y, torch.empty_like(x), 1, bc=bc)
         if len(dims) == 2:
             w3 = inputs.stencil_weights("box", 2, 3, "gaussian", seed=1)
             binding.direct_run(w3, x, y, torch.empty_like(x), 1, bc=bc)
+        if len(dims) == 3 and bc == "periodic":
+            w27 = inputs.stencil_weights("box", 3, 1, "random", seed=1)
+            binding.direct_run(w27, x, y, torch.empty_like(x), 1, bc=bc)
         binding.error_norms(y, x)
         del x, y
         torch.cuda.synchronize()
+    # a batch: four 2048^2 grids, one multi-grid launch per sweep index
+    w = inputs.stencil_weights("box", 2, 3, "gaussian", seed=1)
+    xs = [torch.from_numpy(inputs.uniform01(k, (2048, 2048))).cuda() for k in range(4)]
+    ys = [torch.empty_like(x) for x in xs]
+    plans = [binding.Plan(w, (2048, 2048), dtype="bf16", bc="periodic", fusion_depth=2) for _ in xs]
+    binding.run_batch(plans, xs, ys, [4] * 4)
+    torch.cuda.synchronize()
     assert binding.device_status() == 0
 
 
@@ -686,10 +700,19 @@ def suite_mode():
             except binding.SparStencilError as e:
                 line[f"{dt}_sparse"] = f"unsupported: {e}"
                 continue
-            plan.run(x, y, T)  # fixes the autotuned depth
+            plan.run(x, y, T)  # fixes the autotuned depth (and 2D patch shape)
             ms, med = _time_runs(lambda: plan.run(x, y, T), 3, 1, flush)
             line[f"{dt}_sparse_gstencil_s"] = pts / ms / 1e6
             line[f"{dt}_fusion_depth"] = plan.info().fusion_depth
+            if cfg["ndim"] == 2:
+                line[f"{dt}_patch"] = f"{plan.info().r1}x{plan.info().r2}"
+            if cfg["ndim"] == 3 and plan.info().fusion_depth > 1:
+                # the unfused sweep beside the fused one the search chose
+                p1 = binding.Plan(w, dims, dtype=dt, bc=bc, fusion_depth=1, shape=cfg["shape"])
+                p1.run(x, y, T)
+                ms1, _ = _time_runs(lambda: p1.run(x, y, T), 3, 1, flush)
+                line[f"{dt}_t1_sparse_gstencil_s"] = pts / ms1 / 1e6
+                plan.run(x, y, T)
             if dt.endswith("split"):
                 line[f"{dt}_low_accumulator"] = plan.info().low_accumulator
             if sample is not None:
