@@ -200,9 +200,32 @@ __global__ void __launch_bounds__(256) direct2d_kernel(const __grid_constant__ D
 // 3D), zero weights of the dense cube included (an FMA with weight 0 leaves a finite sum
 // unchanged); the weights are operands from the kernel's constant parameters.
 // ---------------------------------------------------------------------------------------
-constexpr int DSEG = 64;   // 2D: most output rows per warp (fewer when the grid has few columns)
-constexpr int D3SEG = 32;  // 3D: output planes per warp
-constexpr int DWARPS = 4;  // warps per CTA
+#ifndef SPST_D2_PREFETCH
+#define SPST_D2_PREFETCH 0  // 2D, radius >= 2: load input row i + 1 before row i's FMAs
+#endif
+#ifndef SPST_D2_MINB
+#define SPST_D2_MINB 0  // 2D: resident CTAs per SM the register budget must allow (0: no bound)
+#endif
+#if SPST_D2_MINB > 0
+#define SPST_D2_BOUNDS __launch_bounds__(128, SPST_D2_MINB)
+#else
+#define SPST_D2_BOUNDS __launch_bounds__(128)
+#endif
+#ifndef SPST_D3_ROWS_STAR
+#define SPST_D3_ROWS_STAR 3  // 3D radius-1 star: output rows per warp
+#endif
+#ifndef SPST_D3_ROWS_BOX
+#define SPST_D3_ROWS_BOX 3  // 3D radius-1 box: output rows per warp
+#endif
+#ifndef SPST_D3_MINB
+#define SPST_D3_MINB 4  // 3D: resident CTAs per SM the register budget must allow
+#endif
+#ifndef SPST_D3_SEG
+#define SPST_D3_SEG 32  // 3D: most output planes per warp
+#endif
+constexpr int DSEG = 64;   // 2D, radius 1: most output rows per warp (fewer when the grid has few columns)
+constexpr int D3SEG = SPST_D3_SEG;
+constexpr int DWARPS = 4;  // warps per CTA (128 threads)
 
 __device__ __forceinline__ float f4c(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
 
@@ -251,7 +274,7 @@ __device__ __forceinline__ void row_values(const RowLoad<R>& r, bool left_shfl, 
 }
 
 template <int R>
-__global__ void __launch_bounds__(DWARPS * 32) direct2d_reg_kernel(const __grid_constant__ DirectParams p,
+__global__ void SPST_D2_BOUNDS direct2d_reg_kernel(const __grid_constant__ DirectParams p,
                                                                     const float* __restrict__ in,
                                                                     float* __restrict__ out, int seg) {
   constexpr int K = 2 * R + 1;
@@ -280,14 +303,24 @@ __global__ void __launch_bounds__(DWARPS * 32) direct2d_reg_kernel(const __grid_
     if (p.periodic) return in + (r < 0 ? r + H : (r >= H ? r - H : r)) * W;
     return (r >= 0 && r < H) ? in + r * W : nullptr;
   };
-  // (the rows of a K-row block are independent: their loads need no explicit prefetch, and
-  // one measured slower here, 626 -> 511 GStencil/s for the 9-point box at 4096^2)
+  // radius 1: the rows of a K-row block are independent and their loads need no explicit
+  // prefetch (one measured slower, 626 -> 511 GStencil/s for the 9-point box at 4096^2);
+  // larger radii may load row i + 1 before row i's FMAs (SPST_D2_PREFETCH)
+  constexpr bool PF = SPST_D2_PREFETCH && R >= 2;
+  RowLoad<R> nxt;
+  if constexpr (PF) nxt = load_row<R>(row_ptr(0), x, active, left_shfl, right_shfl, xl, xr);
   for (int ib = 0; ib < nrows; ib += K) {
 #pragma unroll
     for (int ii = 0; ii < K; ii++) {
       const int i = ib + ii;  // input row y0 - R + i
       if (i >= nrows) break;
-      const RowLoad<R> cur = load_row<R>(row_ptr(i), x, active, left_shfl, right_shfl, xl, xr);
+      RowLoad<R> cur;
+      if constexpr (PF) {
+        cur = nxt;
+        if (i + 1 < nrows) nxt = load_row<R>(row_ptr(i + 1), x, active, left_shfl, right_shfl, xl, xr);
+      } else {
+        cur = load_row<R>(row_ptr(i), x, active, left_shfl, right_shfl, xl, xr);
+      }
       float s[4 + 2 * R];
       row_values<R>(cur, left_shfl, right_shfl, s);
       // output row y0 + i - R - a takes this row through weight row a (a = -R .. R); its
@@ -313,29 +346,32 @@ __global__ void __launch_bounds__(DWARPS * 32) direct2d_reg_kernel(const __grid_
   }
 }
 
-// 3D, radius 1: warp w of the CTA owns rows y .. y + D3ROWS - 1 (y = (blockIdx.y * DWARPS +
-// w) * D3ROWS) and 128 columns; it walks the D3SEG + 2 input planes of its z segment, taking
-// rows y-1 .. y+D3ROWS of each.  STAR: only the 7 points of the star (the other weights are
-// zero), in the same order; two rows per warp (the dense cube keeps one, for registers).
-template <bool STAR, int D3ROWS = STAR ? 2 : 1>
-__global__ void __launch_bounds__(DWARPS * 32, 4) direct3d_reg_kernel(const __grid_constant__ DirectParams p,
+// 3D, radius 1: warp w of the CTA owns rows y .. y + ROWS - 1 (y = (blockIdx.y * DWARPS + w) *
+// ROWS) and 128 columns; it walks the zseg + 2 input planes of its z segment, taking rows
+// y - 1 .. y + ROWS of each.  Each input row is consumed (its 6 values per lane) and then
+// refilled with the same row of the next plane, so a row's loads are in flight for a whole
+// plane of FMAs.  STAR: only the 7 points of the star (the other weights are zero), in the
+// same order.
+template <bool STAR, int ROWS>
+__global__ void __launch_bounds__(DWARPS * 32, SPST_D3_MINB) direct3d_reg_kernel(const __grid_constant__ DirectParams p,
                                                                     const float* __restrict__ in,
-                                                                    float* __restrict__ out) {
-  constexpr int NR = D3ROWS + 2;  // input rows per plane
+                                                                    float* __restrict__ out, int zseg) {
+  constexpr int NR = ROWS + 2;  // input rows per plane
   const int lane = threadIdx.x & 31;
   const int64_t D = p.D, H = p.H, W = p.W;
   const int64_t xw = (int64_t)blockIdx.x * 128;
-  const int64_t y = ((int64_t)blockIdx.y * DWARPS + (threadIdx.x >> 5)) * D3ROWS;
+  const int64_t y = ((int64_t)blockIdx.y * DWARPS + (threadIdx.x >> 5)) * ROWS;
   if (y >= H) return;  // the whole warp
   const int64_t x = xw + 4 * lane;
   const bool active = x < W;
-  const int64_t z0 = (int64_t)blockIdx.z * D3SEG;
+  const int64_t z0 = (int64_t)blockIdx.z * zseg;
   const bool left_shfl = lane > 0, right_shfl = lane < 31 && x + 4 < W;
   const int64_t xl = x - 4 >= 0 ? x - 4 : (p.periodic ? W - 4 : -1);
   const int64_t xr = x + 4 < W ? x + 4 : (p.periodic ? 0 : -1);
-  // input row d of a plane is y - 1 + d (wrapped once when periodic: H >= 1 and
-  // y + D3ROWS <= H + D3ROWS - 1); rows past the grid's end, or outside a Dirichlet grid, read zeros
-  int64_t ys[NR];
+  // input row d of a plane is y - 1 + d, wrapped when periodic (H >= 1: a row index below
+  // H + ROWS wraps a bounded number of times); rows outside a Dirichlet grid, and the rows
+  // past the grid's end of the last warp, read zeros
+  int yrow[NR];
   bool yin[NR];
 #pragma unroll
   for (int d = 0; d < NR; d++) {
@@ -343,65 +379,67 @@ __global__ void __launch_bounds__(DWARPS * 32, 4) direct3d_reg_kernel(const __gr
     yin[d] = p.periodic || (yy >= 0 && yy < H);
     while (yy < 0) yy += H;
     while (yy >= H) yy -= H;
-    ys[d] = yy;
+    yrow[d] = (int)yy;
   }
-  float acc[3][D3ROWS][4];
+  float acc[3][ROWS][4];
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
-    for (int r = 0; r < D3ROWS; r++)
+    for (int r = 0; r < ROWS; r++)
 #pragma unroll
       for (int j = 0; j < 4; j++) acc[k][r][j] = 0.f;
   // input planes z0 - 1 .. z0 + nout: each wraps at most once
-  const int nout = (int)(D - z0 < D3SEG ? D - z0 : D3SEG);
+  const int nout = (int)(D - z0 < zseg ? D - z0 : zseg);
   const int npl = nout + 2;
-  auto load_plane = [&](int i, RowLoad<1> (&rl)[NR]) {  // input plane z0 - 1 + i
+  auto plane_base = [&](int i) -> const float* {  // input plane z0 - 1 + i, null for zeros
     int64_t z = z0 - 1 + i;
-    bool zin = true;
-    if (p.periodic)
-      z = z < 0 ? z + D : (z >= D ? z - D : z);
-    else
-      zin = z >= 0 && z < D;
+    if (p.periodic) return in + (z < 0 ? z + D : (z >= D ? z - D : z)) * H * W;
+    return (z >= 0 && z < D) ? in + z * H * W : nullptr;
+  };
+  RowLoad<1> cur[NR];
+  {
+    const float* base = plane_base(0);
 #pragma unroll
     for (int d = 0; d < NR; d++)
-      rl[d] = load_row<1>((zin && yin[d]) ? in + (z * H + ys[d]) * W : nullptr, x, active, left_shfl, right_shfl, xl,
-                          xr);
-  };
-  // the loads of the next input plane are issued before this plane's FMAs
-  RowLoad<1> next[NR];
-  load_plane(0, next);
+      cur[d] = load_row<1>((base && yin[d]) ? base + (int64_t)yrow[d] * W : nullptr, x, active, left_shfl, right_shfl, xl, xr);
+  }
   for (int ib = 0; ib < npl; ib += 3) {
 #pragma unroll
     for (int ii = 0; ii < 3; ii++) {
       const int i = ib + ii;  // input plane z0 - 1 + i
       if (i >= npl) break;
-      RowLoad<1> cur[NR];
+      const bool more = i + 1 < npl;
+      const float* nbase = more ? plane_base(i + 1) : nullptr;
 #pragma unroll
-      for (int d = 0; d < NR; d++) cur[d] = next[d];
-      if (i + 1 < npl) load_plane(i + 1, next);
-      float s[NR][6];
+      for (int d = 0; d < NR; d++) {
+        float s[6];
+        row_values<1>(cur[d], left_shfl, right_shfl, s);
+        if (more)
+          cur[d] = load_row<1>((nbase && yin[d]) ? nbase + (int64_t)yrow[d] * W : nullptr, x, active, left_shfl, right_shfl, xl, xr);
+        // input row d reaches output row r through dy = d - r; output plane z0 + i - 1 - a
+        // through dz = a (accumulator slot (i - 1 - a) mod 3)
 #pragma unroll
-      for (int d = 0; d < NR; d++) row_values<1>(cur[d], left_shfl, right_shfl, s[d]);
+        for (int a = -1; a <= 1; a++) {
+          const int slot = ((ii - 1 - a) % 3 + 6) % 3;
 #pragma unroll
-      for (int a = -1; a <= 1; a++) {
-        const int slot = ((ii - 1 - a) % 3 + 6) % 3;
+          for (int r = 0; r < ROWS; r++) {
+            const int dy = d - r;
+            if (dy < 0 || dy > 2) continue;
 #pragma unroll
-        for (int r = 0; r < D3ROWS; r++)
-#pragma unroll
-          for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int dy = 0; dy < 3; dy++)
+            for (int j = 0; j < 4; j++)
 #pragma unroll
               for (int dx = 0; dx < 3; dx++) {
-                const int nz = (a != 0 ? 1 : 0) + (dy != 1 ? 1 : 0) + (dx != 1 ? 1 : 0);
-                if (STAR && nz > 1) continue;
-                acc[slot][r][j] = fmaf(p.wdense[((a + 1) * 3 + dy) * 3 + dx], s[r + dy][j + dx], acc[slot][r][j]);
+                if (STAR && (a != 0) + (dy != 1) + (dx != 1) > 1) continue;
+                acc[slot][r][j] = fmaf(p.wdense[((a + 1) * 3 + dy) * 3 + dx], s[j + dx], acc[slot][r][j]);
               }
+          }
+        }
       }
+      // output plane z0 + i - 2 has now taken its last input plane
       const int done = ((ii - 2) % 3 + 3) % 3;
       const int oz = i - 2;
 #pragma unroll
-      for (int r = 0; r < D3ROWS; r++) {
+      for (int r = 0; r < ROWS; r++) {
         if (oz >= 0 && active && y + r < H)
           *reinterpret_cast<float4*>(out + ((z0 + oz) * H + y + r) * W + x) =
               make_float4(acc[done][r][0], acc[done][r][1], acc[done][r][2], acc[done][r][3]);
@@ -655,78 +693,155 @@ __global__ void band2d_kernel(const BandParams p) {
 // 3D Dirichlet frame of a fused radius-1 sweep of depth t: the cells within bw = t - 1 of a
 // face need step-by-step values (the fused kernel sees the zero boundary only once).  The
 // frame is cut into boxes: z slabs (z < bw or z >= D - bw, all y and x), y slabs (the other
-// z, y < bw or y >= H - bw), x slabs (the other z and y, x < bw or x >= W - bw), each cut into
-// chunks of up to kB3 x kB3 cells across.  A CTA stages its box widened by t cells (zeros
-// outside the grid), takes t FP32 steps in shared memory with the zero boundary re-imposed,
-// FMAs in (dz, dy, dx) order, and writes the box.
+// z, y < bw or y >= H - bw), x slabs (the other z and y, x < bw or x >= W - bw).  A box spans
+// the slab's thickness, band3d_lane(t) cells along its lane axis (x for z and y slabs, y for
+// x slabs) and kB3 cells along its other long axis.  A CTA stages its box widened by t cells
+// (zeros outside the grid) and takes t FP32 steps in shared memory; step s computes only the
+// cells within t - 1 - s of the box that lie inside the grid (the cells outside stay zero:
+// the boundary rule), a warp per row along the lane axis, FMAs in (dz, dy, dx) order (STAR:
+// the 7 points of the star only, the other weights being zero).
 // ---------------------------------------------------------------------------------------
 constexpr int kB3 = 32;
+// box extent along the lane axis: the widest step region (the box widened by t - 1 per side)
+// then spans at most 32 lanes
+__host__ __device__ constexpr int band3d_lane(int t) { return 34 - 2 * t > 8 ? 34 - 2 * t : 8; }
 
-__global__ void band3d_kernel(const Band3DParams p) {
+template <bool STAR>
+__global__ void __launch_bounds__(256) band3d_kernel(const Band3DParams p) {
   allow_next_sweep();
   extern __shared__ float b3[];
-  const int D = p.D, H = p.H, W = p.W, bw = p.bw, t = p.t;
+  const int D = p.D, H = p.H, W = p.W, bw = p.bw, t = p.t, L = band3d_lane(p.t);
+  const int dim[3] = {D, H, W};
   const int zlo = bw < D ? bw : D, zhi0 = (D - bw > zlo) ? D - bw : zlo;  // z slabs [0, zlo), [zhi0, D)
   const int ylo = bw < H ? bw : H, yhi0 = (H - bw > ylo) ? H - bw : ylo;
   const int xlo = bw < W ? bw : W, xhi0 = (W - bw > xlo) ? W - bw : xlo;
   int b = (int)blockIdx.x;
-  int z0, z1, y0, y1, x0, x1;
+  int lo[3], hi[3];  // the box, (z, y, x)
+  int la;            // lane axis: 2 (x) or 1 (y)
   const int nz_slab = p.nzy * p.nzx, ny_slab = p.nyz * p.nyx, nx_slab = p.nxz * p.nxy;
   if (b < 2 * nz_slab) {
     const int s = b / nz_slab, c = b % nz_slab;
-    z0 = s ? zhi0 : 0, z1 = s ? D : zlo;
-    y0 = (c / p.nzx) * kB3, y1 = min(H, y0 + kB3), x0 = (c % p.nzx) * kB3, x1 = min(W, x0 + kB3);
+    lo[0] = s ? zhi0 : 0, hi[0] = s ? D : zlo;
+    lo[1] = (c / p.nzx) * kB3, hi[1] = min(H, lo[1] + kB3);
+    lo[2] = (c % p.nzx) * L, hi[2] = min(W, lo[2] + L);
+    la = 2;
   } else if ((b -= 2 * nz_slab) < 2 * ny_slab) {
     const int s = b / ny_slab, c = b % ny_slab;
-    z0 = zlo + (c / p.nyx) * kB3, z1 = min(zhi0, z0 + kB3);
-    y0 = s ? yhi0 : 0, y1 = s ? H : ylo;
-    x0 = (c % p.nyx) * kB3, x1 = min(W, x0 + kB3);
+    lo[0] = zlo + (c / p.nyx) * kB3, hi[0] = min(zhi0, lo[0] + kB3);
+    lo[1] = s ? yhi0 : 0, hi[1] = s ? H : ylo;
+    lo[2] = (c % p.nyx) * L, hi[2] = min(W, lo[2] + L);
+    la = 2;
   } else {
     b -= 2 * ny_slab;
     if (b >= 2 * nx_slab) return;
     const int s = b / nx_slab, c = b % nx_slab;
-    z0 = zlo + (c / p.nxy) * kB3, z1 = min(zhi0, z0 + kB3);
-    y0 = ylo + (c % p.nxy) * kB3, y1 = min(yhi0, y0 + kB3);
-    x0 = s ? xhi0 : 0, x1 = s ? W : xlo;
+    lo[0] = zlo + (c / p.nxy) * kB3, hi[0] = min(zhi0, lo[0] + kB3);
+    lo[1] = ylo + (c % p.nxy) * L, hi[1] = min(yhi0, lo[1] + L);
+    lo[2] = s ? xhi0 : 0, hi[2] = s ? W : xlo;
+    la = 1;
   }
-  if (z0 >= z1 || y0 >= y1 || x0 >= x1) return;
-  const int wz0 = z0 - t, wy0 = y0 - t, wx0 = x0 - t;
-  const int WD = z1 - z0 + 2 * t, WH = y1 - y0 + 2 * t, WW = x1 - x0 + 2 * t;
-  const int n = WD * WH * WW;
+  if (lo[0] >= hi[0] || lo[1] >= hi[1] || lo[2] >= hi[2]) return;
+  // staged box: cells lo - t .. hi + t - 1 per axis; row pitch odd (conflict-free lanes along y)
+  int w0[3], S[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) w0[a] = lo[a] - t, S[a] = hi[a] - lo[a] + 2 * t;
+  const int sy = S[2] | 1, sz = sy * S[1];
   float* a = b3;
-  float* c = b3 + n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int zz = i / (WH * WW), yy = (i / WW) % WH, xx = i % WW;
-    const int z = wz0 + zz, y = wy0 + yy, x = wx0 + xx;
-    a[i] = (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W)
-               ? p.src[(int64_t)(z + p.src_off) * p.src_plane + (int64_t)(y + p.src_off) * p.src_pitch + x + p.src_off]
-               : 0.f;
+  float* c = b3 + sz * S[0];
+  // staging, kBatch loads in flight per thread.  The source is padded with zeros at least t
+  // cells deep on every side (the launcher checks src_off >= t), so the staged box is read
+  // without bounds checks.  A thread's cell advances by blockDim.x cells per iteration through
+  // mixed-radix carries, its source and shared-memory offsets with it (no division per cell).
+  const int ns = S[0] * S[1] * S[2], S12 = S[1] * S[2];
+  const int nt = (int)blockDim.x;
+  const int adz = nt / S12, adr = nt - adz * S12, ady = adr / S[2], adx = adr - ady * S[2];
+  const int64_t pl = p.src_plane, pi = p.src_pitch;
+  const float* sb = p.src + (int64_t)(w0[0] + p.src_off) * pl + (int64_t)(w0[1] + p.src_off) * pi + w0[2] + p.src_off;
+  int cy, cx;
+  int64_t go;  // source offset of the thread's cell from sb
+  int ko;      // its shared-memory offset
+  {
+    const int cz = (int)threadIdx.x / S12, cr = (int)threadIdx.x - cz * S12;
+    cy = cr / S[2], cx = cr - cy * S[2];
+    go = cz * pl + cy * pi + cx;
+    ko = cz * sz + cy * sy + cx;
+  }
+  const int64_t gstep = adz * pl + ady * pi + adx, gcx = pi - S[2], gcy = pl - S[1] * pi;
+  const int kstep = adz * sz + ady * sy + adx, kcx = sy - S[2], kcy = sz - S[1] * sy;
+  constexpr int kBatch = 8;
+  for (int i0 = threadIdx.x; i0 < ns; i0 += kBatch * nt) {
+    float v[kBatch];
+    int kk[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; u++) {
+      const bool in_box = i0 + u * nt < ns;
+      v[u] = in_box ? sb[go] : 0.f;
+      kk[u] = in_box ? ko : -1;
+      cx += adx, go += gstep, ko += kstep;
+      if (cx >= S[2]) cx -= S[2], cy++, go += gcx, ko += kcx;
+      cy += ady;
+      if (cy >= S[1]) cy -= S[1], go += gcy, ko += kcy;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; u++)
+      if (kk[u] >= 0) {
+        a[kk[u]] = v[u];
+        c[kk[u]] = 0.f;
+      }
   }
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int ra = la == 2 ? 1 : 2;  // the row axis besides z
+  const int lst = la == 2 ? 1 : sy, rst = ra == 2 ? 1 : sy;
   for (int s = 0; s < t; s++) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int zz = i / (WH * WW), yy = (i / WW) % WH, xx = i % WW;
-      const int z = wz0 + zz, y = wy0 + yy, x = wx0 + xx;
-      float v = 0.f;
-      if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W && zz >= 1 && zz < WD - 1 && yy >= 1 &&
-          yy < WH - 1 && xx >= 1 && xx < WW - 1) {
-        const float* q = a + ((zz - 1) * WH + (yy - 1)) * WW + (xx - 1);
+    // step s: the box widened by e = t - 1 - s, clipped to the grid, in staged coordinates
+    const int e = t - 1 - s;
+    int rl[3], nr[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      const int l = max(lo[q] - e, 0), h = min(hi[q] + e, dim[q]);
+      rl[q] = l - w0[q], nr[q] = h - l;
+    }
+    const int nra = ra == 2 ? nr[2] : nr[1], rla = ra == 2 ? rl[2] : rl[1];  // the row axis
+    const int nla = la == 2 ? nr[2] : nr[1], lla = la == 2 ? rl[2] : rl[1];  // the lane axis
+    // warp w takes rows w, w + nwarps, ... of the nr[0] x nra rows (z, then the row axis),
+    // advanced by carries
+    const int rows = nr[0] * nra, rz = nwarps / nra, rr = nwarps - rz * nra;
+    int iz = rl[0] + warp / nra, ir = rla + warp % nra;
+    for (int row = warp; row < rows; row += nwarps, iz += rz, ir += rr) {
+      if (ir >= rla + nra) ir -= nra, iz++;
+      for (int kl = lane; kl < nla; kl += 32) {
+        const int k = iz * sz + ir * rst + (lla + kl) * lst;
+        const float* q = a + k - sz - sy - 1;
+        float v = 0.f;
+#pragma unroll
         for (int dz = 0; dz < 3; dz++)
+#pragma unroll
           for (int dy = 0; dy < 3; dy++)
-            for (int dx = 0; dx < 3; dx++) v = fmaf(p.w[(dz * 3 + dy) * 3 + dx], q[(dz * WH + dy) * WW + dx], v);
+#pragma unroll
+            for (int dx = 0; dx < 3; dx++) {
+              if (STAR && (dz != 1) + (dy != 1) + (dx != 1) > 1) continue;  // a zero weight
+              v = fmaf(p.w[(dz * 3 + dy) * 3 + dx], q[dz * sz + dy * sy + dx], v);
+            }
+        c[k] = v;
       }
-      c[i] = v;
     }
     __syncthreads();
     float* tmp = a;
     a = c;
     c = tmp;
   }
-  const int bd = z1 - z0, bh = y1 - y0, bwid = x1 - x0;
-  for (int i = threadIdx.x; i < bd * bh * bwid; i += blockDim.x) {
-    const int z = z0 + i / (bh * bwid), y = y0 + (i / bwid) % bh, x = x0 + i % bwid;
-    p.dst[(int64_t)(z + p.dst_off) * p.dst_plane + (int64_t)(y + p.dst_off) * p.dst_pitch + x + p.dst_off] =
-        a[((z - wz0) * WH + (y - wy0)) * WW + (x - wx0)];
+  const int bd = hi[0] - lo[0], bh = hi[1] - lo[1], bx = hi[2] - lo[2], bhx = bh * bx;
+  const int odz = nt / bhx, odr = nt - odz * bhx, ody = odr / bx, odx = odr - ody * bx;
+  int oz = (int)threadIdx.x / bhx, orr = (int)threadIdx.x - oz * bhx, oy = orr / bx, ox = orr - oy * bx;
+  for (int i = threadIdx.x; i < bd * bhx; i += nt) {
+    p.dst[(int64_t)(lo[0] + oz + p.dst_off) * p.dst_plane + (int64_t)(lo[1] + oy + p.dst_off) * p.dst_pitch + lo[2] + ox +
+          p.dst_off] = a[(oz + t) * sz + (oy + t) * sy + ox + t];
+    ox += odx;
+    if (ox >= bx) ox -= bx, oy++;
+    oy += ody;
+    if (oy >= bh) oy -= bh, oz++;
+    oz += odz;
   }
 }
 
@@ -759,27 +874,50 @@ __global__ void pad_copy3d_kernel(const float* __restrict__ in, float* __restric
 }
 
 // Periodic ghost shell of a padded 3D grid rewritten from the interior it wraps to (after a
-// sweep that wrote the interior only).  One thread per padded cell of each padded row; rows
-// wholly in the interior only touch their 2G ghost columns.
-__global__ void ghost_refresh3d_kernel(float* __restrict__ g3, int D, int H, int W, int G, int64_t Wp) {
+// sweep that wrote the interior only; needs G <= D, H, W).  Three disjoint sets of ghost cells,
+// each read from interior cells only: whole padded rows of the z ghost planes and the y ghost
+// rows of the interior planes, a warp per row along x; then the 2G x ghost cells of every
+// interior row, a thread per cell.
+__global__ void __launch_bounds__(256) ghost_refresh3d_kernel(float* __restrict__ g3, int D, int H, int W, int G,
+                                                              int64_t Wp) {
   allow_next_sweep();
-  const int64_t Hp = (int64_t)H + 2 * G, Dp = (int64_t)D + 2 * G;
-  const int64_t rows = Dp * Hp;
-  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-    const int64_t yp = r % Hp, zp = r / Hp;
-    const bool ghost_row = yp < G || yp >= H + G || zp < G || zp >= D + G;
-    int64_t z = zp - G, y = yp - G;
+  const int Hp = H + 2 * G, Wr = W + 2 * G;
+  const int64_t plane = (int64_t)Hp * Wp;
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int rows_z = 2 * G * Hp, rows = rows_z + D * 2 * G;
+  for (int r = gw; r < rows; r += nw) {
+    int zp, yp;
+    if (r < rows_z) {
+      const int k = r / Hp;  // ghost plane k: padded plane k (k < G) or D + k
+      yp = r - k * Hp;
+      zp = k < G ? k : D + k;
+    } else {
+      const int q = r - rows_z, zi = q / (2 * G), k = q - zi * 2 * G;
+      zp = G + zi;
+      yp = k < G ? k : H + k;
+    }
+    int z = zp - G, y = yp - G;
     z = z < 0 ? z + D : (z >= D ? z - D : z);
     y = y < 0 ? y + H : (y >= H ? y - H : y);
-    const float* src = g3 + ((z + G) * Hp + (y + G)) * Wp + G;
-    float* dst = g3 + r * Wp;
-    for (int64_t xp = threadIdx.x; xp < (int64_t)W + 2 * G; xp += blockDim.x) {
-      const bool ghost_col = xp < G || xp >= W + G;
-      if (!ghost_row && !ghost_col) continue;
-      int64_t x = xp - G;
+    const float* src = g3 + (z + G) * plane + (int64_t)(y + G) * Wp + G;
+    float* dst = g3 + zp * plane + (int64_t)yp * Wp;
+    for (int xp = lane; xp < Wr; xp += 32) {
+      int x = xp - G;
       x = x < 0 ? x + W : (x >= W ? x - W : x);
       dst[xp] = src[x];
     }
+  }
+  const int64_t ncells = (int64_t)D * H * 2 * G;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / (2 * G);
+    const int k = (int)(i - row * 2 * G);
+    const int64_t zi = row / H, yi = row - zi * H;
+    const int xp = k < G ? k : W + k;
+    int x = xp - G;
+    x = x < 0 ? x + W : x - W;
+    float* rp = g3 + (zi + G) * plane + (yi + G) * Wp;
+    rp[xp] = rp[G + x];
   }
 }
 
@@ -794,9 +932,8 @@ cudaError_t launch_pad_copy3d(const float* in, float* padded, int D, int H, int 
 }
 
 cudaError_t launch_ghost_refresh3d(float* padded, int D, int H, int W, int G, int64_t Wp, cudaStream_t stream) {
-  const int64_t rows = ((int64_t)D + 2 * G) * ((int64_t)H + 2 * G);
-  const int64_t blocks = rows < 152 * 32 ? rows : 152 * 32;
-  ghost_refresh3d_kernel<<<(unsigned)blocks, 128, 0, stream>>>(padded, D, H, W, G, Wp);
+  if (G <= 0) return cudaSuccess;
+  ghost_refresh3d_kernel<<<152 * 4, 256, 0, stream>>>(padded, D, H, W, G, Wp);
   return cudaGetLastError();
 }
 
@@ -826,10 +963,27 @@ static cudaError_t launch_direct2d(const DirectParams& p, const float* in, float
   if (p.W % 4 == 0) {
     // rows per warp: DSEG, fewer when the grid has too few warps for the SMs (about 48 warps
     // per SM); a shorter segment re-reads 2R more rows per segment, mostly from L2
-    const int64_t col_warps = (p.W + 127) / 128;
+    const int64_t col_warps = (p.W + 127) / 128, col_blocks = (p.W + 128 * DWARPS - 1) / (128 * DWARPS);
     int64_t seg = DSEG;
-    while (seg > 8 && col_warps * ((p.H + seg - 1) / seg) < 152 * 48) seg /= 2;
-    dim3 g((unsigned)((p.W + 128 * DWARPS - 1) / (128 * DWARPS)), (unsigned)((p.H + seg - 1) / seg));
+    if (R == 1) {
+      while (seg > 8 && col_warps * ((p.H + seg - 1) / seg) < 152 * 48) seg /= 2;
+    } else {
+      // FMA-bound radii: whole waves of resident CTAs (a partial last wave leaves SMs with
+      // half the warps), segments of 32-128 rows (a segment re-reads 2R rows)
+      static int slots = 0;  // resident CTAs on the device
+      if (slots == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct2d_reg_kernel<R>, DWARPS * 32, 0);
+        slots = sms * (per_sm > 0 ? per_sm : 1);
+      }
+      const int64_t waves = (col_blocks * ((p.H + 127) / 128) + slots - 1) / slots;
+      const int64_t nseg = (int64_t)slots * waves / col_blocks;
+      seg = (p.H + (nseg > 0 ? nseg : 1) - 1) / (nseg > 0 ? nseg : 1);
+      seg = seg < 32 ? 32 : (seg > 128 ? 128 : seg);
+    }
+    dim3 g((unsigned)col_blocks, (unsigned)((p.H + seg - 1) / seg));
     direct2d_reg_kernel<R><<<g, DWARPS * 32, 0, stream>>>(p, in, out, (int)seg);
     return cudaGetLastError();
   }
@@ -870,21 +1024,29 @@ cudaError_t launch_band2d(BandParams p, cudaStream_t stream) {
 cudaError_t launch_band3d(Band3DParams p, cudaStream_t stream) {
   if (p.t < 2 || p.bw <= 0) return cudaSuccess;
   auto cdiv = [](int a, int b) { return a > 0 ? (a + b - 1) / b : 0; };
+  const int L = band3d_lane(p.t);
   const int zmid = p.D - 2 * p.bw > 0 ? p.D - 2 * p.bw : 0, ymid = p.H - 2 * p.bw > 0 ? p.H - 2 * p.bw : 0;
   p.nzy = cdiv(p.H, kB3);
-  p.nzx = cdiv(p.W, kB3);
+  p.nzx = cdiv(p.W, L);
   p.nyz = cdiv(zmid, kB3);
-  p.nyx = cdiv(p.W, kB3);
+  p.nyx = cdiv(p.W, L);
   p.nxz = cdiv(zmid, kB3);
-  p.nxy = cdiv(ymid, kB3);
+  p.nxy = cdiv(ymid, L);
   const int blocks = 2 * (p.nzy * p.nzx + p.nyz * p.nyx + p.nxz * p.nxy);
-  // the largest box: bw x kB3 x kB3 (or kB3 x kB3 x kB3 when bw > kB3), widened by t per side
-  const int e = kB3 + 2 * p.t, thin = (p.bw < kB3 ? p.bw : kB3) + 2 * p.t;
-  const size_t smem = 2 * (size_t)e * e * thin * sizeof(float);
+  // the largest staged box, two buffers: a slab of thickness bw (at most) by kB3 by L, widened
+  // by t per side, with the row pitch rounded up to odd
+  const size_t e = kB3 + 2 * p.t, l = L + 2 * p.t, th = p.bw + 2 * p.t;
+  const size_t zy = th * e * (l | 1), xs = e * l * (th | 1);
+  const size_t smem = 2 * (zy > xs ? zy : xs) * sizeof(float);
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t err = cudaFuncSetAttribute(band3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (p.src_off < p.t) return cudaErrorInvalidValue;  // the staged boxes reach t cells outside
+  bool star = true;  // only the centre and the six axis neighbours are nonzero
+  for (int idx = 0; idx < 27; idx++)
+    if ((idx / 9 != 1) + ((idx / 3) % 3 != 1) + (idx % 3 != 1) > 1 && p.w[idx] != 0.f) star = false;
+  const auto kern = star ? band3d_kernel<true> : band3d_kernel<false>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  if (blocks > 0) band3d_kernel<<<blocks, 256, smem, stream>>>(p);
+  if (blocks > 0) kern<<<blocks, 256, smem, stream>>>(p);
   return cudaGetLastError();
 }
 
@@ -920,13 +1082,17 @@ cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* ou
       const int a = idx / 9, b = (idx / 3) % 3, c = idx % 3;
       if ((a != 1) + (b != 1) + (c != 1) > 1 && p.wdense[idx] != 0.f) star = false;
     }
-    const int rows = star ? 2 : 1;  // output rows per warp (the kernels' D3ROWS)
-    dim3 g((unsigned)((p.W + 127) / 128), (unsigned)((p.H + DWARPS * rows - 1) / (DWARPS * rows)),
-           (unsigned)((p.D + D3SEG - 1) / D3SEG));
+    const int rows = star ? SPST_D3_ROWS_STAR : SPST_D3_ROWS_BOX;  // output rows per warp
+    // planes per warp: D3SEG, halved (down to 8) while the grid has fewer CTAs than one wave
+    // of resident CTAs (SPST_D3_MINB per SM)
+    const int64_t cols = (p.W + 127) / 128, rowb = (p.H + DWARPS * rows - 1) / (DWARPS * rows);
+    int zseg = D3SEG;
+    while (zseg > 8 && cols * rowb * ((p.D + zseg - 1) / zseg) < 152 * SPST_D3_MINB) zseg /= 2;
+    dim3 g((unsigned)cols, (unsigned)rowb, (unsigned)((p.D + zseg - 1) / zseg));
     if (star)
-      direct3d_reg_kernel<true><<<g, DWARPS * 32, 0, stream>>>(p, in, out);
+      direct3d_reg_kernel<true, SPST_D3_ROWS_STAR><<<g, DWARPS * 32, 0, stream>>>(p, in, out, zseg);
     else
-      direct3d_reg_kernel<false><<<g, DWARPS * 32, 0, stream>>>(p, in, out);
+      direct3d_reg_kernel<false, SPST_D3_ROWS_BOX><<<g, DWARPS * 32, 0, stream>>>(p, in, out, zseg);
     return cudaGetLastError();
   }
   if (r == 1) {

@@ -417,6 +417,7 @@ def test_sparse_3d_matches_oracle(torch_cuda, oracle_mod, shape, recipe, dims, s
     ((34, 50, 130), 7, "dirichlet", "bf16_split"),
     ((40, 36, 72), 6, "periodic", "bf16"),           # ghost shell of width 2
     ((17, 20, 66), 5, "periodic", "fp16_split"),
+    ((18, 21, 70), 5, "dirichlet", "bf16"),          # band boxes ragged along every axis
 ])
 def test_sparse_3d_fused_matches_oracle(torch_cuda, oracle_mod, dims, steps, bc, dtype):
     """3D radius-1 star fused two steps per sweep (one halo stage in shared memory); zero
