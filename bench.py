@@ -994,6 +994,7 @@ def serve_trace(n_jobs=512, budget=120 << 30, slots=8):
             "capacity_gstencil_s": cap / 1e9, "completed": st.completed, "failed": st.failed,
             "p50_s": st.p50_s, "p99_s": st.p99_s, "mean_s": st.mean_s, "max_s": st.max_s,
             "throughput_gstencil_s": st.gstencil_per_s, "peak_device_bytes": st.peak_bytes,
+            "pool_high_bytes": st.pool_high_bytes, "pool_resident_bytes": st.pool_reserved_bytes,
             "alone_equals_mix": same, "alone_checked": checked,
             "wall_s": time.perf_counter() - t_start}
 

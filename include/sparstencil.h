@@ -312,12 +312,15 @@ sparstencil_status sparstencil_trace_read(uint64_t* out, int n);
  * Serving: a request loop over the library (not in the paper; the runtime that takes
  * stencil jobs as they arrive).  A dispatcher thread admits jobs in arrival order when one
  * of `slots` execution slots (CUDA streams) is free and the job's device bytes fit under
- * `hbm_budget_bytes` next to the jobs running; each admitted job copies its grid in, runs and
- * copies its result out on its own stream, side by side with the others, and releases its
- * slot and bytes when its last copy completes.  A job that can never fit the budget fails
- * with SPST_ERR_NOMEM.  Plans are pooled by stencil and grid and reused by later jobs.
- * 2D and 3D jobs run the sparse tensor-core path (sparstencil_run).  Results equal those of
- * the same job run alone.
+ * `hbm_budget_bytes` next to the jobs running; each admitted job copies its grid in (unless
+ * it is already on the device), runs and copies its result out (unless it stays on the
+ * device) on its own stream, side by side with the others, and releases its slot and bytes
+ * when its work completes.  A job that can never fit the budget fails with SPST_ERR_NOMEM.
+ * Plans are pooled by stencil and grid and reused by later jobs; the server's device
+ * allocations come from a memory pool of its own that keeps up to the budget resident
+ * between jobs (no allocation reaches the driver once the pool has grown).  2D and 3D jobs
+ * run the sparse tensor-core path (sparstencil_run).  Results equal those of the same job
+ * run alone.
  * --------------------------------------------------------------------------------------- */
 typedef struct sparstencil_server_s* sparstencil_server_t;
 
@@ -334,10 +337,16 @@ typedef struct {
   int64_t timesteps;
   const float* in_host;      /* host grid, read when the job is admitted (keep it valid until
                                 the job completes); page-locked memory lets the copies of
-                                different jobs overlap */
-  float* out_host;           /* host result, written before the job is reported complete */
+                                different jobs overlap; NULL when in_device is given */
+  float* out_host;           /* host result, written before the job is reported complete;
+                                NULL when out_device is given */
   double arrival_s;          /* arrival time on the server clock (sparstencil_server_clock);
                                 negative: the time of submission */
+  const float* in_device;    /* device grid resident across jobs (caller-owned, ready when the
+                                job is submitted, unchanged until it completes): read in place,
+                                no host copy; NULL when in_host is given */
+  float* out_device;         /* device grid that receives the result in place (caller-owned,
+                                not aliasing in_device); NULL when out_host is given */
 } sparstencil_job;
 
 typedef struct {
@@ -352,13 +361,18 @@ typedef struct {
   double p50_s, p99_s, mean_s, max_s;  /* latency (completion - arrival) of completed jobs */
   size_t peak_bytes;                   /* largest sum of admitted jobs' bytes */
   double gstencil_per_s;               /* completed point-steps / (last completion - first arrival) */
+  size_t pool_reserved_bytes;          /* device memory the server's pool holds resident now */
+  size_t pool_high_bytes;              /* the most it has held */
 } sparstencil_server_summary;
 
 /* Starts a server on the current device.  slots in 1..64. */
 sparstencil_status sparstencil_server_create(size_t hbm_budget_bytes, int slots, sparstencil_server_t* out);
 /* Seconds since the server started (the clock of arrival_s and the results). */
 double sparstencil_server_clock(sparstencil_server_t server);
-/* Queues a job (plans it on the host now); *job_id receives its id.  Thread-safe. */
+/* Queues a job (plans it on the host now); *job_id receives its id.  Exactly one of in_host
+ * and in_device, and one of out_host and out_device, must be given (SPST_ERR_INVALID
+ * otherwise).  A job's device bytes (counted against the budget) are the grids the server
+ * allocates for it (one per host-side grid) plus the plan's workspace.  Thread-safe. */
 sparstencil_status sparstencil_server_submit(sparstencil_server_t server, const sparstencil_job* job,
                                              int64_t* job_id);
 /* Waits up to timeout_s for a job to finish; SPST_ERR_TIMEOUT if it has not. */

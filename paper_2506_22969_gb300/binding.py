@@ -45,7 +45,8 @@ class Job(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int), ("radius", ctypes.c_int), ("weights", ctypes.c_void_p),
                 ("ndim", ctypes.c_int), ("dims", ctypes.c_void_p), ("dtype", ctypes.c_int), ("bc", ctypes.c_int),
                 ("fusion_depth", ctypes.c_int), ("timesteps", ctypes.c_int64), ("in_host", ctypes.c_void_p),
-                ("out_host", ctypes.c_void_p), ("arrival_s", ctypes.c_double)]
+                ("out_host", ctypes.c_void_p), ("arrival_s", ctypes.c_double), ("in_device", ctypes.c_void_p),
+                ("out_device", ctypes.c_void_p)]
 
 
 class JobResult(ctypes.Structure):
@@ -56,7 +57,8 @@ class JobResult(ctypes.Structure):
 class ServerSummary(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("mean_s", ctypes.c_double),
-                ("max_s", ctypes.c_double), ("peak_bytes", ctypes.c_size_t), ("gstencil_per_s", ctypes.c_double)]
+                ("max_s", ctypes.c_double), ("peak_bytes", ctypes.c_size_t), ("gstencil_per_s", ctypes.c_double),
+                ("pool_reserved_bytes", ctypes.c_size_t), ("pool_high_bytes", ctypes.c_size_t)]
 
 
 EXPORTS = ["sparstencil_plan", "sparstencil_plan_set_layout", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host",
@@ -342,22 +344,27 @@ class Server:
     def clock(self) -> float:
         return load().sparstencil_server_clock(self.handle)
 
-    def submit(self, weights, in_host, out_host, steps, dtype="bf16", bc="periodic", fusion_depth=1,
+    def submit(self, weights, grid_in, grid_out, steps, dtype="bf16", bc="periodic", fusion_depth=1,
                shape="box", arrival_s=-1.0) -> int:
-        """in_host / out_host: contiguous float32 numpy arrays or CPU torch tensors (page-locked
-        memory lets jobs' copies overlap); the server keeps references until the job is waited."""
+        """grid_in / grid_out: contiguous float32 numpy arrays or CPU torch tensors (host grids,
+        copied by the server; page-locked memory lets jobs' copies overlap), or CUDA float32
+        tensors (device grids resident across jobs, read and written in place: the input must
+        be ready when the job is submitted).  The server keeps references until the job is
+        waited."""
         w = np.ascontiguousarray(weights, dtype=np.float32)
         ndim = w.ndim
-        shp = tuple(in_host.shape)
-        if len(shp) != ndim or tuple(out_host.shape) != shp:
+        shp = tuple(grid_in.shape)
+        if len(shp) != ndim or tuple(grid_out.shape) != shp:
             raise ValueError("grid rank or shape mismatch")
         d = np.asarray(shp, dtype=np.int64)
+        in_h, in_d = _grid_ptrs(grid_in)
+        out_h, out_d = _grid_ptrs(grid_out)
         job = Job(_code(_SHAPES, shape), (w.shape[0] - 1) // 2, w.ctypes.data, ndim, d.ctypes.data,
                   _code(_DTYPES, dtype), _code(_BCS, bc), int(fusion_depth), int(steps),
-                  _host_ptr(in_host), _host_ptr(out_host), float(arrival_s))
+                  in_h, out_h, float(arrival_s), in_d, out_d)
         jid = ctypes.c_int64()
         _check(load().sparstencil_server_submit(self.handle, ctypes.byref(job), ctypes.byref(jid)))
-        self._keep[jid.value] = (in_host, out_host)
+        self._keep[jid.value] = (grid_in, grid_out)
         return jid.value
 
     def wait(self, job_id: int, timeout_s: float = 600.0) -> JobResult:
@@ -387,18 +394,17 @@ class Server:
             pass
 
 
-def _host_ptr(a):
+def _grid_ptrs(a):
+    """(host pointer, device pointer) of a serving job's grid, one of them None."""
     try:
         import torch
-        if isinstance(a, torch.Tensor):
-            if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
-                raise TypeError("host grids must be contiguous float32 CPU tensors")
-            return a.data_ptr()
-    except ImportError:
+        if isinstance(a, torch.Tensor) and a.is_cuda:
+            if a.dtype != torch.float32 or not a.is_contiguous():
+                raise TypeError("device grids must be contiguous float32 CUDA tensors")
+            return None, a.data_ptr()
+    except ImportError:  # pragma: no cover
         pass
-    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
-        raise TypeError("host grids must be contiguous float32 arrays")
-    return a.ctypes.data
+    return _host_ptr(a), None
 
 
 def server_simulate(budget: int, slots: int, arrival_s, duration_s, nbytes):

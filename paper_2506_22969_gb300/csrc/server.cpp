@@ -3,11 +3,14 @@
 // Jobs (a stencil, a grid on the host, a step count) arrive over time.  A dispatcher thread
 // admits them in arrival order as execution slots (CUDA streams) and device memory under an
 // HBM budget become free, so that work submitted while other jobs are on the GPU joins them
-// there: each admitted job copies its grid in, runs its sweeps and copies the result out on
-// its own stream, side by side with the others.  Plans are kept per stencil signature and
-// reused by later jobs (a plan holds device tables and a workspace, so one plan serves one
-// job at a time).  2D and 3D jobs run the sparse tensor-core path.  Latencies (completion
-// minus arrival) give p50/p99.
+// there: each admitted job copies its grid in (unless it is already on the device), runs its
+// sweeps and copies the result out (unless it stays on the device) on its own stream, side by
+// side with the others.  Plans are kept per stencil signature and reused by later jobs (a
+// plan holds device tables and a workspace, so one plan serves one job at a time).  The
+// server's grids and workspaces come from a stream-ordered memory pool of its own whose
+// release threshold is the budget, so memory freed by a job stays resident for the next.
+// 2D and 3D jobs run the sparse tensor-core path.  Latencies (completion minus arrival) give
+// p50/p99.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,6 +65,8 @@ struct Job {
   int64_t steps = 0;
   const float* in_host = nullptr;
   float* out_host = nullptr;
+  const float* in_dev = nullptr;  // caller-owned device grids (resident across jobs)
+  float* out_dev = nullptr;
   double arrival = 0, admitted = -1, done = -1;
   size_t bytes = 0;
   int status = SPST_OK;
@@ -109,6 +114,7 @@ struct sparstencil_server_s {
   std::multimap<std::string, sparstencil_plan_t> idle_plans;
   std::vector<cudaStream_t> streams;
   std::vector<char> slot_busy;
+  cudaMemPool_t pool = nullptr;  // the server's device allocations (release threshold: the budget)
   int64_t next_id = 1;
   int64_t submitted = 0, completed = 0, failed = 0;
   int64_t point_steps = 0;
@@ -120,9 +126,10 @@ struct sparstencil_server_s {
   double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 
   // Takes the job's plan (an idle one of the same stencil and grid, else a new one: host
-  // planning only) and returns the device bytes the job holds while it runs: its grids in
-  // and out plus the plan's workspace.  The planner tables kept on the device by pooled
-  // plans are small and not counted.
+  // planning only) and returns the device bytes the job holds while it runs: the grids the
+  // server allocates for it (input and output unless the caller's are on the device) plus the
+  // plan's workspace.  The planner tables kept on the device by pooled plans are small and
+  // not counted.
   size_t take_plan(Job& j, sparstencil_status* st) {
     const size_t grid = (size_t)cells(j) * sizeof(float);
     *st = SPST_OK;
@@ -137,7 +144,7 @@ struct sparstencil_server_s {
       if (*st != SPST_OK) return 0;
     }
     j.ws_bytes = sparstencil_workspace_bytes(j.plan);
-    return 2 * grid + j.ws_bytes;
+    return (j.in_dev ? 0 : grid) + (j.out_dev ? 0 : grid) + j.ws_bytes;
   }
 
   void start_job(const std::shared_ptr<Job>& jp) {
@@ -149,21 +156,26 @@ struct sparstencil_server_s {
     cudaStream_t s = streams[slot];
     const size_t grid = (size_t)cells(j) * sizeof(float);
     sparstencil_status st = SPST_OK;
-    if (cudaMallocAsync((void**)&j.d_in, grid, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&j.d_out, grid, s) != cudaSuccess)
+    auto alloc = [&](void** p, size_t n) { return cudaMallocFromPoolAsync(p, n, pool, s) == cudaSuccess; };
+    float* own_in = nullptr;
+    float* own_out = nullptr;
+    if ((!j.in_dev && !alloc((void**)&own_in, grid)) || (!j.out_dev && !alloc((void**)&own_out, grid)))
       st = SPST_ERR_NOMEM;
-    if (st == SPST_OK && cudaMemcpyAsync(j.d_in, j.in_host, grid, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    j.d_in = j.in_dev ? const_cast<float*>(j.in_dev) : own_in;
+    j.d_out = j.out_dev ? j.out_dev : own_out;
+    if (st == SPST_OK && own_in && cudaMemcpyAsync(own_in, j.in_host, grid, cudaMemcpyHostToDevice, s) != cudaSuccess)
       st = SPST_ERR_CUDA;
     if (st == SPST_OK) {
       // the workspace is the job's, stream-ordered like its grids, and leaves with it
-      if (cudaMallocAsync(&j.d_ws, j.ws_bytes, s) != cudaSuccess) st = SPST_ERR_NOMEM;
+      if (!alloc(&j.d_ws, j.ws_bytes)) st = SPST_ERR_NOMEM;
       if (st == SPST_OK) st = sparstencil_bind_workspace(j.plan, j.d_ws, j.ws_bytes, s);
       if (st == SPST_OK) st = sparstencil_run(j.plan, j.d_in, j.d_out, j.steps, s);
     }
-    if (st == SPST_OK && cudaMemcpyAsync(j.out_host, j.d_out, grid, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (st == SPST_OK && own_out &&
+        cudaMemcpyAsync(j.out_host, own_out, grid, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       st = SPST_ERR_CUDA;
-    cudaFreeAsync(j.d_in, s);
-    cudaFreeAsync(j.d_out, s);
+    if (own_in) cudaFreeAsync(own_in, s);
+    if (own_out) cudaFreeAsync(own_out, s);
     if (j.d_ws) cudaFreeAsync(j.d_ws, s);
     if (cudaEventCreateWithFlags(&j.finished, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventRecord(j.finished, s) != cudaSuccess)
@@ -253,12 +265,25 @@ sparstencil_status sparstencil_server_create(size_t hbm_budget_bytes, int slots,
   if (cudaGetDevice(&s->device) != cudaSuccess) return spst::report_error(SPST_ERR_CUDA, "cudaGetDevice failed");
   s->policy.budget = hbm_budget_bytes;
   s->policy.slots = slots;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = s->device;
+  if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess)
+    return spst::report_error(SPST_ERR_CUDA, "memory pool creation failed");
+  uint64_t keep = hbm_budget_bytes;  // memory freed by a job stays in the pool up to the budget
+  if (cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+    cudaMemPoolDestroy(s->pool);
+    return spst::report_error(SPST_ERR_CUDA, "memory pool threshold failed");
+  }
   s->streams.assign(slots, nullptr);
   s->slot_busy.assign(slots, 0);
   for (auto& st : s->streams)
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       for (auto x : s->streams)
         if (x) cudaStreamDestroy(x);
+      cudaMemPoolDestroy(s->pool);
       return spst::report_error(SPST_ERR_CUDA, "stream creation failed");
     }
   sparstencil_server_s* raw = s.get();
@@ -271,8 +296,12 @@ double sparstencil_server_clock(sparstencil_server_t server) { return server ? s
 
 sparstencil_status sparstencil_server_submit(sparstencil_server_t server, const sparstencil_job* job,
                                              int64_t* job_id) {
-  if (!server || !job || !job->weights || !job->dims || !job->in_host || !job->out_host)
+  if (!server || !job || !job->weights || !job->dims)
     return spst::report_error(SPST_ERR_INVALID, "null server, job or job pointer");
+  if (!job->in_host == !job->in_device || !job->out_host == !job->out_device)
+    return spst::report_error(SPST_ERR_INVALID, "give exactly one of in_host / in_device and of out_host / out_device");
+  if (job->in_device && (const void*)job->in_device == (const void*)job->out_device)
+    return spst::report_error(SPST_ERR_INVALID, "in_device and out_device must not alias");
   if (job->ndim != 2 && job->ndim != 3) return spst::report_error(SPST_ERR_UNSUPPORTED, "ndim must be 2 or 3");
   if (job->timesteps < 0 || job->radius < 1) return spst::report_error(SPST_ERR_INVALID, "bad steps or radius");
   auto jp = std::make_shared<Job>();
@@ -291,6 +320,8 @@ sparstencil_status sparstencil_server_submit(sparstencil_server_t server, const 
   j.steps = job->timesteps;
   j.in_host = job->in_host;
   j.out_host = job->out_host;
+  j.in_dev = job->in_device;
+  j.out_dev = job->out_device;
   std::lock_guard<std::mutex> lk(server->mu);
   if (server->stop) return spst::report_error(SPST_ERR_INVALID, "server is shutting down");
   sparstencil_status st = SPST_OK;
@@ -359,6 +390,11 @@ sparstencil_status sparstencil_server_stats(sparstencil_server_t server, sparste
   out->peak_bytes = server->peak_bytes;
   const double span = server->last_done - server->first_arrival;
   out->gstencil_per_s = span > 0 ? (double)server->point_steps / span / 1e9 : 0;
+  uint64_t cur = 0, high = 0;
+  cudaMemPoolGetAttribute(server->pool, cudaMemPoolAttrReservedMemCurrent, &cur);
+  cudaMemPoolGetAttribute(server->pool, cudaMemPoolAttrReservedMemHigh, &high);
+  out->pool_reserved_bytes = (size_t)cur;
+  out->pool_high_bytes = (size_t)high;
   return SPST_OK;
 }
 
@@ -370,8 +406,10 @@ sparstencil_status sparstencil_server_destroy(sparstencil_server_t server) {
   }
   server->cv_work.notify_all();
   if (server->worker.joinable()) server->worker.join();
+  for (auto s : server->streams) cudaStreamSynchronize(s);
   for (auto& kv : server->idle_plans) sparstencil_plan_destroy(kv.second);
   for (auto s : server->streams) cudaStreamDestroy(s);
+  cudaMemPoolDestroy(server->pool);
   delete server;
   return SPST_OK;
 }
