@@ -243,11 +243,14 @@ def test_direct_fp32_ragged(torch_cuda, oracle_mod, dims, r, bc):
     assert l2 <= 1e-6 and linf <= 1e-5, (l2, linf)
 
 
-@pytest.mark.parametrize("dims,bc", [((5, 12, 132), "periodic"), ((37, 9, 260), "dirichlet"), ((33, 20, 36), "periodic")])
-def test_direct_fp32_3d_ragged(torch_cuda, oracle_mod, dims, bc):
-    """The 3D radius-1 comparator with fewer planes than a warp's segment and ragged widths."""
+@pytest.mark.parametrize("shape,dims,bc", [("box", (5, 12, 132), "periodic"), ("box", (37, 9, 260), "dirichlet"),
+                                           ("box", (33, 20, 36), "periodic"), ("star", (37, 10, 260), "periodic"),
+                                           ("star", (9, 13, 36), "dirichlet")])
+def test_direct_fp32_3d_ragged(torch_cuda, oracle_mod, shape, dims, bc):
+    """The 3D radius-1 comparator (box and star kernels, three rows per warp) with fewer planes
+    than a warp's segment, row counts not a multiple of a warp's rows, and ragged widths."""
     torch = torch_cuda
-    w = inputs.stencil_weights("box", 3, 1, "random", seed=10)
+    w = inputs.stencil_weights(shape, 3, 1, "random", seed=10)
     u = inputs.uniform_pm1(4, dims)
     x = torch.from_numpy(u).cuda()
     out, work = torch.empty_like(x), torch.empty_like(x)
