@@ -168,6 +168,16 @@ sparstencil_status sparstencil_run(sparstencil_plan_t plan, const float* in, flo
 sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in_host, float* out_host,
                                         int64_t timesteps, cudaStream_t stream);
 
+/* Same as sparstencil_run_host, but asynchronous: the host-to-device copy into the plan's
+ * staging grid, the sweeps and the device-to-host copy are queued on `stream` (copies on the
+ * copy engines) and the call returns without synchronising, so that runs of several plans
+ * on several streams overlap one run's copies with another's sweeps.  in_host and out_host
+ * must stay valid (and out_host unread) until `stream` has passed the run; page-locked
+ * memory makes the copies asynchronous.  A plan holds one staging pair: at most one run of
+ * a plan may be in flight (runs of one plan on one stream are ordered by the stream). */
+sparstencil_status sparstencil_run_host_async(sparstencil_plan_t plan, const float* in_host, float* out_host,
+                                              int64_t timesteps, cudaStream_t stream);
+
 /* Same as sparstencil_run, but records CUDA events before and after the copy into the
  * padded grid and after the last sweep, and synchronises `stream` before returning:
  *   copy_in_ms:  device time of the copy into the padded grid (may be NULL)

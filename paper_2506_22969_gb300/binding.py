@@ -62,6 +62,7 @@ class ServerSummary(ctypes.Structure):
 
 
 EXPORTS = ["sparstencil_plan", "sparstencil_plan_set_layout", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host",
+           "sparstencil_run_host_async",
            "sparstencil_run_noalloc", "sparstencil_plan_destroy",
            "sparstencil_workspace_bytes", "sparstencil_bind_workspace", "sparstencil_run_batch", "sparstencil_query",
            "sparstencil_plan_tables", "sparstencil_table_kpad", "sparstencil_direct_run", "sparstencil_error_norms",
@@ -87,6 +88,7 @@ def load():
     lib.sparstencil_plan.argtypes = [i32, i32, vp, i32, vp, i32, i32, i32, ctypes.POINTER(vp)]
     lib.sparstencil_run.argtypes = [vp, vp, vp, i64, vp]
     lib.sparstencil_run_host.argtypes = [vp, vp, vp, i64, vp]
+    lib.sparstencil_run_host_async.argtypes = [vp, vp, vp, i64, vp]
     lib.sparstencil_run_profiled.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
     lib.sparstencil_run_noalloc.argtypes = [vp, vp, vp, i64, vp]
     lib.sparstencil_plan_destroy.argtypes = [vp]
@@ -241,6 +243,14 @@ class Plan:
         """Host FP32 grids (numpy arrays or CPU tensors, ideally pinned)."""
         _check(load().sparstencil_run_host(self._h, ctypes.c_void_p(_host_ptr(x_host)),
                                            ctypes.c_void_p(_host_ptr(out_host)), int(steps), _stream_ptr(stream)))
+        return out_host
+
+    def run_host_async(self, x_host, out_host, steps: int, stream=None):
+        """Queues a host-buffer run on `stream` without waiting (sparstencil_run_host_async):
+        keep both buffers alive and out_host unread until the stream has passed it."""
+        _check(load().sparstencil_run_host_async(self._h, ctypes.c_void_p(_host_ptr(x_host)),
+                                                 ctypes.c_void_p(_host_ptr(out_host)), int(steps),
+                                                 _stream_ptr(stream)))
         return out_host
 
     def tables(self, which: int = 0, remainder_depth: int = 0):

@@ -1257,8 +1257,12 @@ sparstencil_status sparstencil_run_profiled(sparstencil_plan_t plan, const float
   return SPST_OK;
 }
 
-sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in_host, float* out_host,
-                                        int64_t timesteps, cudaStream_t stream) {
+namespace {
+// Host-buffer run: H2D into the plan's staging grid (or, when `zero_copy` and the input is
+// page-locked memory the device can address, the copy-in kernel reads it directly), the
+// sweeps, D2H from the staging output; synchronises the stream when `sync`.
+sparstencil_status run_host_impl(sparstencil_plan_t plan, const float* in_host, float* out_host, int64_t timesteps,
+                                 cudaStream_t stream, bool zero_copy, bool sync) {
   if (!plan || !in_host || !out_host) return fail(SPST_ERR_INVALID, "null plan or grid");
   if (timesteps < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
   sparstencil_status s = ensure_device(plan, stream);
@@ -1270,13 +1274,10 @@ sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in
       return fail(SPST_ERR_NOMEM, "staging allocation failed");
     }
   }
-  // Page-locked host memory that the device can address (cudaHostAlloc / cudaHostRegister)
-  // is read by the copy-in kernel itself, which saves the staging copy; other host memory
-  // is copied to the device first.
   const float* src = plan->stage_in;
   cudaPointerAttributes at;
-  if (timesteps > 0 && cudaPointerGetAttributes(&at, in_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
-      at.devicePointer)
+  if (zero_copy && timesteps > 0 && cudaPointerGetAttributes(&at, in_host) == cudaSuccess &&
+      at.type == cudaMemoryTypeHost && at.devicePointer)
     src = (const float*)at.devicePointer;
   else
     cudaGetLastError();
@@ -1285,8 +1286,22 @@ sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in
   s = run_sweeps(plan, src, plan->stage_out, timesteps, stream);
   if (s != SPST_OK) return s;
   SPST_CUDA(cudaMemcpyAsync(out_host, plan->stage_out, bytes, cudaMemcpyDeviceToHost, stream), "D2H");
-  SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
+  if (sync) SPST_CUDA(cudaStreamSynchronize(stream), "stream sync");
   return SPST_OK;
+}
+}  // namespace
+
+sparstencil_status sparstencil_run_host(sparstencil_plan_t plan, const float* in_host, float* out_host,
+                                        int64_t timesteps, cudaStream_t stream) {
+  // page-locked input that the device can address is read by the copy-in kernel itself,
+  // which saves the staging copy of a lone run
+  return run_host_impl(plan, in_host, out_host, timesteps, stream, true, true);
+}
+
+sparstencil_status sparstencil_run_host_async(sparstencil_plan_t plan, const float* in_host, float* out_host,
+                                              int64_t timesteps, cudaStream_t stream) {
+  // the copies go through the copy engines, so that they overlap other streams' sweeps
+  return run_host_impl(plan, in_host, out_host, timesteps, stream, false, false);
 }
 
 sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const float* const* in, float* const* out,

@@ -294,6 +294,29 @@ def test_run_host_equals_run(torch_cuda):
     np.testing.assert_array_equal(host_out.numpy(), y.cpu().numpy())
 
 
+def test_run_host_async_pipelined_equals_run(torch_cuda):
+    """Asynchronous host-buffer runs of two plans alternating on two streams (the pipelined
+    end-to-end mode): every run's result equals the device-buffer run of its input."""
+    torch = torch_cuda
+    w = inputs.stencil_weights("box", 2, 3, "gaussian", seed=3)
+    dims = (520, 390)
+    plans = [binding.Plan(w, dims, dtype="bf16_split", bc="periodic", fusion_depth=2) for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    us = [inputs.uniform01(20 + i, dims) for i in range(6)]
+    hin = [torch.from_numpy(u).pin_memory() for u in us]
+    hout = [torch.full(dims, float("nan")).pin_memory() for _ in us]
+    for i in range(len(us)):
+        plans[i % 2].run_host_async(hin[i], hout[i], 7, stream=streams[i % 2])
+    torch.cuda.synchronize()
+    for i, u in enumerate(us):
+        x = torch.from_numpy(u).cuda()
+        y = torch.empty_like(x)
+        plans[0].run(x, y, 7)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(hout[i].numpy(), y.cpu().numpy())
+    assert binding.device_status() == 0
+
+
 def test_full_size_box9_sampled(torch_cuda, oracle_mod):
     """Box-2D9P 4096^2, periodic, 100 steps (the benchmark workload): sampled points against
     the dependence-cone oracle, both precisions, in the launch configuration the bench times."""
