@@ -199,8 +199,8 @@ sparstencil_status sparstencil_run_profiled(sparstencil_plan_t plan, const float
  * padded cells per grid, e.g. a 2040 x 2040 grid with ghost width 4) and 512 KiB of
  * planner tables.  Larger grids are rejected with SPST_ERR_UNSUPPORTED and a message.
  * It calls no cudaMalloc, cudaFree or allocating library routine; the first call on a
- * device resolves the arrays' device addresses (cudaGetSymbolAddress) and should come
- * before any stream capture.  All calls share the arrays: each call clears what must
+ * device resolves the arrays' device addresses (cudaGetSymbolAddress).  All calls share the
+ * arrays: each call clears what must
  * start at zero and uploads the plan's tables from host memory (cudaMemcpyAsync on
  * `stream`), and calls that overlap on the GPU race.  2D sparse plans only.  The plan
  * runs at the depth sparstencil_query reports: a plan made with fusion_depth 0 that no
