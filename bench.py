@@ -381,6 +381,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="config C5 (Poisson-arrival job server) and exit")
     ap.add_argument("--ncu-kernels", action="store_true",
                     help="profiling case: one launch or two of every kernel of the library, then exit")
+    ap.add_argument("--correction", action="store_true",
+                    help="run time and accuracy of the optional FP64 correction step against its period")
     ap.add_argument("--ablation", action="store_true",
                     help="dense versus sparse tensor-core MMAs on Box-2D49P at several sizes and exit")
     args = ap.parse_args()
@@ -390,6 +392,8 @@ def main():
         return batch_mode()
     if args.serve:
         return serve_mode()
+    if args.correction:
+        return correction_mode()
     if args.ablation:
         return ablation_mode()
     if args.ncu_kernels:
@@ -673,6 +677,13 @@ def _rel_l2_gpu(binding, x, ref):
     return l2, linf
 
 
+def _rel(vals, ref):
+    """(rel-L2, rel-Linf) of sampled values against their reference values."""
+    d = np.asarray(vals, dtype=np.float64) - np.asarray(ref, dtype=np.float64)
+    r = np.asarray(ref, dtype=np.float64)
+    return float(np.sqrt(np.sum(d * d) / np.sum(r * r))), float(np.max(np.abs(d)) / np.max(np.abs(r)))
+
+
 def suite_mode():
     """Configs C1, C3, C4a/b and the 1D workloads: GStencil/s of the sparse path (single and split, fusion depth
     autotuned) and of the plain FP32 direct kernel, with rel-L2 against the FP64 oracle (C1:
@@ -852,6 +863,53 @@ def _c4c_jobs(n=64, seed=4):
         w = inputs.stencil_weights(shape, 2, 3, "gaussian", seed=seed)
         jobs.append((shape, w, (int(sides[i]), int(sides[i])), 200))
     return jobs
+
+
+def correction_mode():
+    """The optional FP64 correction step (every k-th time step in FP64 on the CUDA cores): run
+    time and accuracy against k.  Box-2D9P 4096^2, 100 steps, BF16 single and split words at
+    t = 6, rel-L2 / rel-Linf against the FP32 direct result; Heat-1D 10,240,000, 1000 steps,
+    BF16 single words at t = 8, against 8 points of the FP64 oracle (the 1D FP32 direct kernel
+    itself drifts by about 1e-6 there).  One JSON line per workload and precision."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2506_22969_gb300 import binding, inputs
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    cases = (("box2d9p_4096", "bf16", 6, 100), ("box2d9p_4096", "bf16_split", 6, 100), ("heat1d", "bf16", 8, 1000))
+    for name, dtype, t, T in cases:
+        cfg = inputs.CONFIGS[name]
+        dims = cfg["dims"]
+        nd = len(dims)
+        w = inputs.stencil_weights(cfg["shape"], nd, cfg["radius"], cfg["recipe"], seed=cfg["seed"])
+        u = inputs.make_grid(cfg["grid"], cfg["seed"], dims)
+        x = torch.from_numpy(u).cuda()
+        y = torch.empty_like(x)
+        pts = T * int(np.prod(dims))
+        line = {"workload": f"{cfg['name'].split(',')[0]}, {cfg['bc']}, {T} steps", "dtype": dtype, "fusion_depth": t}
+        if nd == 1:
+            rng = np.random.default_rng(3)
+            sample = [(int(v),) for v in rng.integers(0, dims[0], 8)]
+            ref = oracle.points(u, w, cfg["bc"], T, sample)
+        else:
+            ref_t, work = torch.empty_like(x), torch.empty_like(x)
+            binding.direct_run(w, x, ref_t, work, T, bc=cfg["bc"])
+        for k in (0, 50, 10, 2, 1):
+            plan = binding.Plan(w, dims, dtype=dtype, bc=cfg["bc"], fusion_depth=t, shape=cfg["shape"])
+            plan.set_fp64_correction(k)
+            plan.run(x, y, T)
+            ms, _ = _time_runs(lambda: plan.run(x, y, T), 2, 1, flush)
+            if nd == 1:
+                got = y.cpu().numpy()
+                l2, linf = _rel(np.array([float(got[s]) for s in sample]), ref)
+            else:
+                l2, linf = _rel_l2_gpu(binding, y, ref_t)
+            line[f"k{k}"] = {"gstencil_s": pts / ms / 1e6, "ms_per_run": ms, "rel_l2": l2, "rel_linf": linf}
+            del plan
+        print(json.dumps(line), flush=True)
+        del x, y
+        torch.cuda.empty_cache()
 
 
 def batch_mode():

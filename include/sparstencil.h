@@ -79,6 +79,8 @@ typedef struct {
   int pairing;         /* column pairs of the 2:4 conversion: 0 = Algorithm 1 (Sec. 3.2), 1 = a
                           maximum matching on the stencil's actual support, taken when the
                           support is smaller than the box and that needs fewer K chunks */
+  int fp64_every;      /* k of the FP64 correction step (0: off; see
+                          sparstencil_plan_set_fp64_correction) */
 } sparstencil_plan_info;
 
 /* Builds a plan for `shape` stencils of radius `radius` on an ndim grid (1, 2 or 3) of extents dims.
@@ -208,6 +210,17 @@ sparstencil_status sparstencil_run_profiled(sparstencil_plan_t plan, const float
  * no depths). */
 sparstencil_status sparstencil_run_noalloc(sparstencil_plan_t plan, const float* in, float* out, int64_t timesteps,
                                            cudaStream_t stream);
+
+/* Optional FP64 correction step (not in the paper's method): with every_k = k >= 1, time
+ * steps k, 2k, 3k, ... of each run are each computed by one CUDA-core step in FP64
+ * arithmetic from the FP32 state (every nonzero weight times its input summed in FP64 in
+ * (dz, dy, dx) order, rounded once to FP32), and the k - 1 steps between them by the plan's
+ * tensor-core sweeps (fused as usual, with a remainder sweep where k - 1 is not a multiple
+ * of the depth).  every_k = 1 runs every step in FP64; 0 (the default) turns it off.
+ * sparstencil_run, _run_host, _run_host_async and _run_profiled honour it;
+ * sparstencil_run_batch and sparstencil_run_noalloc reject such plans with
+ * SPST_ERR_UNSUPPORTED.  Errors: SPST_ERR_INVALID (null plan, every_k < 0). */
+sparstencil_status sparstencil_plan_set_fp64_correction(sparstencil_plan_t plan, int every_k);
 
 /* Releases the plan and every device buffer the library allocated for it. */
 sparstencil_status sparstencil_plan_destroy(sparstencil_plan_t plan);

@@ -38,7 +38,7 @@ class PlanInfo(ctypes.Structure):
                 ("tile_outputs", ctypes.c_int), ("num_tiles", ctypes.c_int64), ("planner_ms", ctypes.c_double),
                 ("ghost", ctypes.c_int), ("tile_pitch", ctypes.c_int), ("tile_rows", ctypes.c_int),
                 ("bank_conflicts", ctypes.c_int), ("low_accumulator", ctypes.c_int),
-                ("dense_ablation", ctypes.c_int), ("pairing", ctypes.c_int)]
+                ("dense_ablation", ctypes.c_int), ("pairing", ctypes.c_int), ("fp64_every", ctypes.c_int)]
 
 
 class Job(ctypes.Structure):
@@ -62,7 +62,7 @@ class ServerSummary(ctypes.Structure):
 
 
 EXPORTS = ["sparstencil_plan", "sparstencil_plan_set_layout", "sparstencil_run", "sparstencil_run_profiled", "sparstencil_run_host",
-           "sparstencil_run_host_async",
+           "sparstencil_run_host_async", "sparstencil_plan_set_fp64_correction",
            "sparstencil_run_noalloc", "sparstencil_plan_destroy",
            "sparstencil_workspace_bytes", "sparstencil_bind_workspace", "sparstencil_run_batch", "sparstencil_query",
            "sparstencil_plan_tables", "sparstencil_table_kpad", "sparstencil_direct_run", "sparstencil_error_norms",
@@ -93,6 +93,7 @@ def load():
     lib.sparstencil_run_noalloc.argtypes = [vp, vp, vp, i64, vp]
     lib.sparstencil_plan_destroy.argtypes = [vp]
     lib.sparstencil_plan_set_low_accumulator.argtypes = [vp, i32]
+    lib.sparstencil_plan_set_fp64_correction.argtypes = [vp, i32]
     lib.sparstencil_plan_set_dense_ablation.argtypes = [vp, i32]
     lib.sparstencil_plan_set_layout.argtypes = [vp, i32, i32]
     lib.sparstencil_cost_model.argtypes = [vp, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -200,6 +201,11 @@ class Plan:
         """sparstencil_plan_set_low_accumulator: split terms after A_hi B_hi go to a TMEM
         accumulator of their own (before the first run)."""
         _check(load().sparstencil_plan_set_low_accumulator(self._h, 1 if enable else 0))
+
+    def set_fp64_correction(self, every_k: int):
+        """sparstencil_plan_set_fp64_correction: every k-th time step of a run in FP64 on the
+        CUDA cores (0: off)."""
+        _check(load().sparstencil_plan_set_fp64_correction(self._h, int(every_k)))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -19,9 +19,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsparstencil.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-CU_SOURCES = ["sweep2d.cu", "aux.cu", "noalloc.cu"]
+CU_SOURCES = ["sweep2d.cu", "aux.cu", "noalloc.cu", "correction.cu"]
 CPP_SOURCES = ["planner.cpp", "capi.cpp", "server.cpp"]
-HEADERS = ["kernels.h", "planner.h"]
+HEADERS = ["kernels.h", "planner.h", "correction.h"]
 
 
 def _cuda_home() -> str:

@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "correction.h"
 #include "kernels.h"
 #include "planner.h"
 
@@ -118,6 +119,7 @@ struct sparstencil_plan_s {
   sparstencil_boundary bc;
   int requested_t = 1, t = 1, t_max = 1;
   bool lo_acc = false;  // split operands: low-order MMA terms in an accumulator of their own
+  int fp64_every = 0;   // k > 0: every k-th time step of a run is an FP64 CUDA-core step
   bool dense = false;   // the dense-MMA ablation (uncompressed A', dense tcgen05 MMAs)
   bool autotune_pending = false;  // fusion_depth 0: t (and the layout) chosen by timing at the first run
   spst::Pairing pairing_pref = spst::Pairing::Auto;  // column pairing of the 2:4 conversion
@@ -716,6 +718,39 @@ sparstencil_status autotune_depth(sparstencil_plan_t p, const float* in, cudaStr
   return SPST_OK;
 }
 
+// Parameters of the FP64 correction step on the plan's padded grids.
+spst::Fp64StepParams fp64_params(sparstencil_plan_t p) {
+  const PlanGeometry& g = p->geo;
+  spst::Fp64StepParams f;
+  std::memset(&f, 0, sizeof(f));
+  f.ndim = g.ndim;
+  f.D = g.ndim == 3 ? g.D : 1;
+  f.H = g.ndim >= 2 ? g.H : 1;
+  f.W = g.W;
+  f.G = g.G;
+  f.Wp = g.Wp;
+  f.Hp = g.ndim == 3 ? g.Hp : 1;
+  f.periodic = p->bc == SPST_PERIODIC ? 1 : 0;
+  const int r = p->radius, side = 2 * r + 1;
+  const int nz = g.ndim == 3 ? side : 1, ny = g.ndim >= 2 ? side : 1;
+  for (int a = 0; a < nz; a++)
+    for (int b = 0; b < ny; b++)
+      for (int c = 0; c < side; c++) {
+        const double w = p->w64[((size_t)a * ny + b) * side + c];
+        if (w == 0.0) continue;
+        f.off[f.npts][0] = g.ndim == 3 ? a - r : 0;
+        f.off[f.npts][1] = g.ndim >= 2 ? b - r : 0;
+        f.off[f.npts][2] = c - r;
+        f.w[f.npts] = w;
+        f.npts++;
+      }
+  if (f.npts == 0) {  // all weights zero: one zero term keeps the kernel's sum defined
+    f.npts = 1;
+    f.w[0] = 0.0;
+  }
+  return f;
+}
+
 sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out, int64_t T, cudaStream_t stream,
                               LaunchTimer* timer = nullptr) {
   sparstencil_status s = ensure_device(p, stream);
@@ -725,16 +760,36 @@ sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out,
     return SPST_OK;
   }
   if (p->autotune_pending && (s = autotune_depth(p, in, stream)) != SPST_OK) return s;
-  std::vector<int> sweeps((size_t)(T / p->t), p->t);
-  if (T % p->t) sweeps.push_back((int)(T % p->t));
+  // the run's operations: tensor-core sweeps of p->t steps (and remainder sweeps), and with
+  // the FP64 correction on, an FP64 step (depth 0 here) in place of every k-th time step
+  std::vector<int> sweeps;
+  auto add_sweeps = [&](int64_t n) {
+    for (int64_t i = 0; i < n / p->t; i++) sweeps.push_back(p->t);
+    if (n % p->t) sweeps.push_back((int)(n % p->t));
+  };
+  if (p->fp64_every > 0) {
+    const int64_t k = p->fp64_every;
+    for (int64_t done = 0; done < T;) {
+      const int64_t tc = std::min<int64_t>(k - 1, T - done);
+      add_sweeps(tc);
+      done += tc;
+      if (done < T) {
+        sweeps.push_back(0);
+        done++;
+      }
+    }
+  } else {
+    add_sweeps(T);
+  }
   int* status = spst::device_status_word();
   if (!status) return fail(SPST_ERR_CUDA, "device status word unavailable");
   // Every table upload is enqueued before the copy-in kernel: a sweep reads its tables
   // during its set-up, which may overlap the previous kernel (programmatic dependent launch),
   // so no upload may sit between two sweeps.
-  std::vector<const SweepTables*> tabs(sweeps.size());
-  std::vector<DeviceTables*> dtabs(sweeps.size());
+  std::vector<const SweepTables*> tabs(sweeps.size(), nullptr);
+  std::vector<DeviceTables*> dtabs(sweeps.size(), nullptr);
   for (size_t i = 0; i < sweeps.size(); i++) {
+    if (sweeps[i] == 0) continue;  // an FP64 step
     std::string err;
     tabs[i] = tables_for(p, sweeps[i], &err);
     if (!tabs[i]) return fail(SPST_ERR_UNSUPPORTED, err);
@@ -752,8 +807,17 @@ sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out,
   SPST_CUDA(copy_in(p, in, p->pad(0), T, stream, p->maxabs), "pad copy");
   if (timer && (s = timer->record(stream)) != SPST_OK) return s;
   int cur = 0;
+  int tc_sweeps = 0;
   for (size_t i = 0; i < sweeps.size(); i++) {
     const bool last = (i + 1 == sweeps.size());
+    if (sweeps[i] == 0) {
+      SPST_CUDA(spst::launch_fp64_step(fp64_params(p), p->pad(cur), last ? nullptr : p->pad(1 - cur),
+                                       last ? out : nullptr, stream),
+                "FP64 step launch");
+      cur = 1 - cur;
+      continue;
+    }
+    tc_sweeps++;
     spst::Sweep2DParams prm = sweep_params(p, *tabs[i], *dtabs[i], status);
     set_output(p, &prm, p->pad(1 - cur), out, last);
     SPST_CUDA(spst::launch_sweep2d(p->tmap[cur], prm, p->num_sms, stream), "sweep launch");
@@ -763,7 +827,7 @@ sparstencil_status run_sweeps(sparstencil_plan_t p, const float* in, float* out,
   // one event after all sweeps: an event between two sweeps would stop the next one from
   // overlapping its set-up with the previous one (programmatic dependent launch)
   if (timer) {
-    timer->sweeps = (int)sweeps.size();
+    timer->sweeps = tc_sweeps;
     if ((s = timer->record(stream)) != SPST_OK) return s;
   }
   return SPST_OK;
@@ -803,6 +867,7 @@ sparstencil_status run_plan_with_buffers(sparstencil_plan_t p, const float* in, 
   if (!p || !in || !out) return fail(SPST_ERR_INVALID, "null plan or grid");
   if (T < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
   if (in == out) return fail(SPST_ERR_INVALID, "in and out must not alias");
+  if (p->fp64_every > 0) return fail(SPST_ERR_UNSUPPORTED, "the allocation-free run does not take the FP64 correction step");
   int dev = 0, major = 0, minor = 0, sms = 0;
   SPST_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   SPST_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev), "device attribute");
@@ -1131,6 +1196,13 @@ sparstencil_status sparstencil_plan(sparstencil_shape shape, int radius, const f
   return SPST_OK;
 }
 
+sparstencil_status sparstencil_plan_set_fp64_correction(sparstencil_plan_t plan, int every_k) {
+  if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
+  if (every_k < 0) return fail(SPST_ERR_INVALID, "every_k must be >= 0");
+  plan->fp64_every = every_k;
+  return SPST_OK;
+}
+
 sparstencil_status sparstencil_plan_set_low_accumulator(sparstencil_plan_t plan, int enable) {
   if (!plan) return fail(SPST_ERR_INVALID, "plan is null");
   if (enable && !is_split(plan->dtype)) return fail(SPST_ERR_INVALID, "the low-order accumulator needs a split dtype");
@@ -1310,6 +1382,7 @@ sparstencil_status sparstencil_run_batch(const sparstencil_plan_t* plans, const 
   if (n == 0) return SPST_OK;
   for (int i = 0; i < n; i++) {
     if (!plans[i] || !in[i] || !out[i]) return fail(SPST_ERR_INVALID, "null plan or grid in the batch");
+    if (plans[i]->fp64_every > 0) return fail(SPST_ERR_UNSUPPORTED, "batched plans cannot take the FP64 correction step");
     if (steps[i] < 0) return fail(SPST_ERR_INVALID, "timesteps must be >= 0");
     if (in[i] == out[i]) return fail(SPST_ERR_INVALID, "in and out must not alias");
     for (int j = 0; j < i; j++)
@@ -1414,6 +1487,7 @@ sparstencil_status sparstencil_query(sparstencil_plan_t plan, sparstencil_plan_i
   info->low_accumulator = plan->lo_acc ? 1 : 0;
   info->dense_ablation = plan->dense ? 1 : 0;
   info->pairing = plan->full.pairing;
+  info->fp64_every = plan->fp64_every;
   return SPST_OK;
 }
 

@@ -695,3 +695,50 @@ def test_widest_stencils_match_oracle(torch_cuda, oracle_mod, ndim, shape, r, di
     l2, linf = oracle_mod.rel_errors(got, ref)
     assert np.all(np.isfinite(got))
     _assert_tol(l2, linf, dtype, plan.info().kpad)
+
+
+@pytest.mark.parametrize("ndim,shape,r,dims,bc,dtype,t,k,steps", [
+    (2, "box", 1, (300, 260), "periodic", "bf16_split", 3, 1, 7),     # every step in FP64
+    (2, "box", 1, (300, 260), "dirichlet", "bf16_split", 3, 4, 17),   # sweeps of 3, bands, FP64 every 4th step
+    (2, "star", 3, (260, 300), "periodic", "fp16_split", 2, 5, 13),
+    (3, "star", 1, (20, 40, 70), "dirichlet", "fp16_split", 2, 3, 8),
+    (3, "box", 1, (20, 24, 72), "periodic", "bf16_split", 1, 2, 6),   # ghost shell written by both kinds of step
+    (1, "box", 2, (40000,), "periodic", "bf16_split", 8, 5, 23),
+])
+def test_fp64_correction_matches_oracle(torch_cuda, oracle_mod, ndim, shape, r, dims, bc, dtype, t, k, steps):
+    """The optional FP64 correction step: every k-th time step on the CUDA cores in FP64, the
+    others in tensor-core sweeps (remainder sweeps between the FP64 steps).  With k = 1 every
+    step is FP64 and the result is within the FP32 rounding of the stored state of the oracle;
+    otherwise within the split tolerance."""
+    torch = torch_cuda
+    recipe = "gaussian" if r == 3 else "random"
+    w = inputs.stencil_weights(shape, ndim, r, recipe, seed=13)
+    u = inputs.uniform_pm1(9, dims) if ndim == 3 else inputs.uniform01(9, dims)
+    plan = binding.Plan(w, dims, dtype=dtype, bc=bc, fusion_depth=t, shape=shape)
+    plan.set_fp64_correction(k)
+    assert plan.info().fp64_every == k
+    x = torch.from_numpy(u).cuda()
+    y = torch.full_like(x, float("nan"))
+    plan.run(x, y, steps)
+    torch.cuda.synchronize()
+    assert binding.device_status() == 0
+    got = y.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    l2, linf = oracle_mod.rel_errors(got, oracle_mod.run(u, w, bc, steps))
+    if k == 1:
+        assert l2 <= 1e-6 and linf <= 1e-5, (l2, linf)
+    else:
+        _assert_tol(l2, linf, dtype)
+
+
+def test_fp64_correction_rejected_by_batch_and_noalloc(torch_cuda):
+    torch = torch_cuda
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=1)
+    plan = binding.Plan(w, (128, 128), dtype="bf16", bc="periodic", fusion_depth=1)
+    plan.set_fp64_correction(3)
+    x = torch.zeros(128, 128, device="cuda")
+    y = torch.empty_like(x)
+    with pytest.raises(binding.SparStencilError):
+        binding.run_batch([plan], [x], [y], [4])
+    with pytest.raises(binding.SparStencilError):
+        plan.run_noalloc(x, y, 4)

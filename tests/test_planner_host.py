@@ -26,7 +26,7 @@ def lib():
 def test_library_exports_every_declared_symbol(lib):
     with open(os.path.join(ROOT, "include", "sparstencil.h")) as f:
         text = f.read()
-    declared = set(re.findall(r"\b(sparstencil_[a-z_]+)\s*\(", text))
+    declared = set(re.findall(r"\b(sparstencil_[a-z0-9_]+)\s*\(", text))
     assert len(declared) >= 15
     for name in declared:
         assert hasattr(lib, name), name
@@ -646,3 +646,17 @@ def test_lut_emulation_3d_reproduces_oracle_step(lib, oracle_mod, bc, shape):
     got = _emulate_sweep_3d(plan, tb, u, bc, dense)
     ref = oracle_mod.run(u, w.astype(np.float64), bc, 1)
     np.testing.assert_array_equal(got, ref)
+
+
+def test_fp64_correction_setting(lib):
+    """The FP64 correction step's period is recorded in the plan (0 turns it off) and a
+    negative period is rejected."""
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=1)
+    plan = binding.Plan(w, (256, 256), dtype="bf16_split", bc="periodic", fusion_depth=3)
+    assert plan.info().fp64_every == 0
+    plan.set_fp64_correction(5)
+    assert plan.info().fp64_every == 5
+    plan.set_fp64_correction(0)
+    assert plan.info().fp64_every == 0
+    with pytest.raises(binding.SparStencilError):
+        plan.set_fp64_correction(-1)
