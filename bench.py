@@ -266,8 +266,8 @@ def ncu_kernels_case():
     3D band), the 1D sweep (Heat-1D 2^26, BF16 split, t = 8, two sweeps with the ghost refresh
     between them), the 2D sweep with 8 x 16 patches
     and the Dirichlet band of a fused 2D sweep (Heat-2D 8192^2, t = 3), a batch launch of four
-    grids, the FP32 direct kernels (1D, 2D radius 1 and 3, 3D radius-1 star and box) and the
-    FP64 error norms."""
+    grids, the FP32 direct kernels (1D, 2D radius 1 and 3, 3D radius-1 star and box), two FP64
+    correction steps (Box-2D9P 4096^2) and the FP64 error norms."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -292,6 +292,16 @@ def ncu_kernels_case():
         binding.error_norms(y, x)
         del x, y
         torch.cuda.synchronize()
+    # the FP64 correction step: two steps of the 9-point box on 4096^2, both in FP64 (the first
+    # writes the padded ping-pong grid, the second the caller's grid)
+    w = inputs.stencil_weights("box", 2, 1, "random", seed=1)
+    x = torch.from_numpy(inputs.uniform01(1, (4096, 4096))).cuda()
+    y = torch.empty_like(x)
+    plan = binding.Plan(w, (4096, 4096), dtype="bf16", bc="periodic", fusion_depth=1)
+    plan.set_fp64_correction(1)
+    plan.run(x, y, 2)
+    torch.cuda.synchronize()
+    del x, y, plan
     # a batch: four 2048^2 grids, one multi-grid launch per sweep index
     w = inputs.stencil_weights("box", 2, 3, "gaussian", seed=1)
     xs = [torch.from_numpy(inputs.uniform01(k, (2048, 2048))).cuda() for k in range(4)]
