@@ -969,7 +969,8 @@ static cudaError_t launch_direct2d(const DirectParams& p, const float* in, float
       while (seg > 8 && col_warps * ((p.H + seg - 1) / seg) < 152 * 48) seg /= 2;
     } else {
       // FMA-bound radii: whole waves of resident CTAs (a partial last wave leaves SMs with
-      // half the warps), segments of 32-128 rows (a segment re-reads 2R rows)
+      // half the warps), segments of 8-128 rows (a segment re-reads 2R rows; small grids take
+      // short segments to give every SM work)
       static int slots = 0;  // resident CTAs on the device
       if (slots == 0) {
         int dev = 0, sms = 0, per_sm = 0;
@@ -981,7 +982,7 @@ static cudaError_t launch_direct2d(const DirectParams& p, const float* in, float
       const int64_t waves = (col_blocks * ((p.H + 127) / 128) + slots - 1) / slots;
       const int64_t nseg = (int64_t)slots * waves / col_blocks;
       seg = (p.H + (nseg > 0 ? nseg : 1) - 1) / (nseg > 0 ? nseg : 1);
-      seg = seg < 32 ? 32 : (seg > 128 ? 128 : seg);
+      seg = seg < 8 ? 8 : (seg > 128 ? 128 : seg);
     }
     dim3 g((unsigned)col_blocks, (unsigned)((p.H + seg - 1) / seg));
     direct2d_reg_kernel<R><<<g, DWARPS * 32, 0, stream>>>(p, in, out, (int)seg);
