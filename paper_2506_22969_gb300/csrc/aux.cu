@@ -223,6 +223,9 @@ __global__ void __launch_bounds__(256) direct2d_kernel(const __grid_constant__ D
 #ifndef SPST_D3_SEG
 #define SPST_D3_SEG 32  // 3D: most output planes per warp
 #endif
+#ifndef SPST_D3_FILL
+#define SPST_D3_FILL 1  // 3D: waves of resident CTAs the z segments are shortened to fill
+#endif
 constexpr int DSEG = 64;   // 2D, radius 1: most output rows per warp (fewer when the grid has few columns)
 constexpr int D3SEG = SPST_D3_SEG;
 constexpr int DWARPS = 4;  // warps per CTA (128 threads)
@@ -1084,11 +1087,11 @@ cudaError_t launch_direct_step(const DirectParams& p, const float* in, float* ou
       if ((a != 1) + (b != 1) + (c != 1) > 1 && p.wdense[idx] != 0.f) star = false;
     }
     const int rows = star ? SPST_D3_ROWS_STAR : SPST_D3_ROWS_BOX;  // output rows per warp
-    // planes per warp: D3SEG, halved (down to 8) while the grid has fewer CTAs than one wave
-    // of resident CTAs (SPST_D3_MINB per SM)
+    // planes per warp: D3SEG, halved (down to 8) while the grid has fewer CTAs than
+    // SPST_D3_FILL waves of resident CTAs (SPST_D3_MINB per SM)
     const int64_t cols = (p.W + 127) / 128, rowb = (p.H + DWARPS * rows - 1) / (DWARPS * rows);
     int zseg = D3SEG;
-    while (zseg > 8 && cols * rowb * ((p.D + zseg - 1) / zseg) < 152 * SPST_D3_MINB) zseg /= 2;
+    while (zseg > 8 && cols * rowb * ((p.D + zseg - 1) / zseg) < 152 * SPST_D3_MINB * SPST_D3_FILL) zseg /= 2;
     dim3 g((unsigned)cols, (unsigned)rowb, (unsigned)((p.D + zseg - 1) / zseg));
     if (star)
       direct3d_reg_kernel<true, SPST_D3_ROWS_STAR><<<g, DWARPS * 32, 0, stream>>>(p, in, out, zseg);
