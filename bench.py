@@ -13,7 +13,8 @@ tensor-core sweeps).
   accuracy  rel-L2 and rel-Linf of the timed run's output at 64 sampled points (random,
             tile corners, grid corners) against the FP64 oracle's dependence cones
   e2e       the same metric through the host-buffer entry points (pinned host buffers, H2D copy of
-            the input and D2H copy of the result inside the timed region)
+            the input and D2H copy of the result inside the timed region; consecutive runs
+            pipelined over two plans and two streams, and one run at a time as serial_value)
   roofline  the sweep kernel's algorithmic HBM bytes (8 B per output per sweep) over its
             device time (CUDA events around the sweeps of a run), against the measured copy
             bandwidth in MEASURED_PEAKS.json
@@ -23,6 +24,11 @@ tensor-core sweeps).
             same workload (same sampled points), and Box-2D9P 4096^2 (100 steps)
   cpu_baseline / --impl reference   the FP64 C oracle on the host cores, on a bounded
             sample of the workload (test infrastructure, not the product path)
+
+Other modes: --suite (every workload configuration, sparse against FP32), --batch (64 grids in
+one multi-grid launch per sweep index), --serve (the C5 trace alone), --ablation (dense vs
+sparse tensor-core MMAs), --correction (the optional FP64 correction step against its
+period), --ncu-case / --ncu-kernels (profiling cases).
 
 --gpus N runs under torchrun with one process per GPU: every rank runs its own replica of
 the workload (the paper's method is single-GPU; replicas only), value = all ranks' work /
